@@ -1,0 +1,709 @@
+/*
+ * oracle.c -- plain CPU oracle (fp64, single thread).  TEST INFRASTRUCTURE:
+ * loaded only by the tests, the smoke check and the benchmark's CPU-baseline
+ * leg.  It shares no code with the CUDA library.  Build: gcc -O2 -std=c11
+ * -ffp-contract=off (no FMA contraction, so the jittered coordinates are
+ * reproducible bit for bit from their defining expression).
+ *
+ * The problem (paper Sec. 2.2): Laplace's equation Delta u = 0 on the unit
+ * square/cube with u = g on the boundary, discretised with P1 (the paper's
+ * linear case, whose 2D/3D weights are the cotangent formula of Sec. 2.2) or
+ * P2 Lagrange elements (the polynomial-degree study of Sec. 4.2, Table 7).
+ * The stiffness matrix is K_ij = sum_T int_T grad(phi_i).grad(phi_j); the
+ * Dirichlet dofs are eliminated, leaving the SPD system K_II u = -K_IB g_B,
+ * which is solved by CG with the Jacobi preconditioner M = diag(K_II)
+ * (preconditioned Krylov solve, Sec. 2.1) to the relative residual of Eq. (2).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ RNG -- */
+/* SplitMix64: state advances by the golden-ratio increment gamma; each state
+ * is passed through the mix64 finaliser (shift-xor, multiply, twice). */
+static const uint64_t GAMMA = 0x9E3779B97F4A7C15ULL;
+
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_rng_u64(uint64_t key, uint64_t i) { return mix64(key + (i + 1) * GAMMA); }
+
+uint64_t orc_rng_key(uint64_t seed, uint32_t stream) {
+    return (seed << 40) ^ ((uint64_t)stream << 32);
+}
+
+/* uniform double in [0,1) from the top 53 bits */
+static double u01(uint64_t r) { return (double)(r >> 11) * 0x1p-53; }
+
+/* --------------------------------------------------------------- system -- */
+struct orc_sys {
+    int dim, degree, cells, jitter, diag_mode;
+    uint64_t seed;
+    int V;          /* vertices per side: cells+1 */
+    int S;          /* dof-lattice points per side: degree*cells+1 */
+    int64_t nv, ndof, nel;
+    int nvert_el;   /* dim+1 */
+    int nloc;       /* dofs per element */
+    double *vx;     /* nv*dim */
+    double *dx;     /* ndof*dim */
+    int32_t *elv;   /* nel*nvert_el vertex ids */
+    int32_t *eld;   /* nel*nloc dof ids: vertices first, then edges (a,b), a<b */
+    int32_t *free_of_full, *bnd_of_full, *full_of_free, *full_of_bnd;
+    int64_t nfree, nbnd;
+    /* assembled (selected rows) */
+    int64_t nnz_full, nnz_ii, nnz_ib;
+    int64_t *rp_full, *rp_ii, *rp_ib;
+    int32_t *ci_full, *ci_ii, *ci_ib;
+    double *v_full, *v_ii, *v_ib;
+};
+
+static void free_assembly(orc_sys *s) {
+    free(s->rp_full); free(s->ci_full); free(s->v_full);
+    free(s->rp_ii); free(s->ci_ii); free(s->v_ii);
+    free(s->rp_ib); free(s->ci_ib); free(s->v_ib);
+    s->rp_full = s->rp_ii = s->rp_ib = NULL;
+    s->ci_full = s->ci_ii = s->ci_ib = NULL;
+    s->v_full = s->v_ii = s->v_ib = NULL;
+    s->nnz_full = s->nnz_ii = s->nnz_ib = 0;
+}
+
+void orc_free(orc_sys *s) {
+    if (!s) return;
+    free_assembly(s);
+    free(s->vx); free(s->dx); free(s->elv); free(s->eld);
+    free(s->free_of_full); free(s->bnd_of_full); free(s->full_of_free); free(s->full_of_bnd);
+    free(s);
+}
+
+/* local edge list of a simplex: (a,b) with a<b in lexicographic order */
+static const int EDGES2[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+static const int EDGES3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+/* Kuhn split of a cube: one tetrahedron per ordering of the three axes; the
+ * path v000 -> +e_p0 -> +e_p1 -> +e_p2 = v111. */
+static const int KUHN[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uint64_t seed) {
+    if ((dim != 2 && dim != 3) || (degree != 1 && degree != 2) || cells < 1) return NULL;
+    if (dim == 3 && jitter) return NULL; /* 3D meshes are regular Kuhn lattices */
+    orc_sys *s = (orc_sys *)calloc(1, sizeof(orc_sys));
+    s->dim = dim; s->degree = degree; s->cells = cells; s->jitter = jitter;
+    s->diag_mode = diag_mode; s->seed = seed;
+    s->V = cells + 1;
+    s->S = degree * cells + 1;
+    s->nv = 1; s->ndof = 1;
+    for (int d = 0; d < dim; ++d) { s->nv *= s->V; s->ndof *= s->S; }
+    s->nvert_el = dim + 1;
+    s->nloc = degree == 1 ? dim + 1 : (dim == 2 ? 6 : 10);
+    int64_t ncell = 1;
+    for (int d = 0; d < dim; ++d) ncell *= cells;
+    s->nel = ncell * (dim == 2 ? 2 : 6);
+
+    /* vertex coordinates: lattice point i/cells, interior points of a jittered
+     * mesh moved by (2u-1)*0.25h per coordinate, u from streams 0 (x) and 1 (y),
+     * counter = vertex id. */
+    s->vx = (double *)malloc(sizeof(double) * s->nv * dim);
+    const uint64_t kx = orc_rng_key(seed, 0), ky = orc_rng_key(seed, 1);
+    const double q = 0.25 / (double)cells;
+    for (int64_t v = 0; v < s->nv; ++v) {
+        int64_t t = v;
+        int idx[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) { idx[d] = (int)(t % s->V); t /= s->V; }
+        int interior = 1;
+        for (int d = 0; d < dim; ++d) if (idx[d] == 0 || idx[d] == cells) interior = 0;
+        for (int d = 0; d < dim; ++d) {
+            double x = (double)idx[d] / (double)cells;
+            if (jitter && interior && d < 2) {
+                uint64_t r = orc_rng_u64(d == 0 ? kx : ky, (uint64_t)v);
+                double dd = 2.0 * u01(r) - 1.0;
+                x = x + dd * q;
+            }
+            s->vx[v * dim + d] = x;
+        }
+    }
+
+    /* elements */
+    s->elv = (int32_t *)malloc(sizeof(int32_t) * s->nel * s->nvert_el);
+    s->eld = (int32_t *)malloc(sizeof(int32_t) * s->nel * s->nloc);
+    const uint64_t kf = orc_rng_key(seed, 2);
+    int64_t e = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        int ci[3] = {0, 0, 0};
+        int64_t t = c;
+        for (int d = 0; d < dim; ++d) { ci[d] = (int)(t % cells); t /= cells; }
+        if (dim == 2) {
+            int32_t v00 = ci[0] + s->V * ci[1];
+            int32_t v10 = v00 + 1, v01 = v00 + s->V, v11 = v00 + s->V + 1;
+            int flip = 0;
+            if (diag_mode == 1) flip = (orc_rng_u64(kf, (uint64_t)c) >> 63) == 0; /* u < 1/2 */
+            int32_t tri[2][3];
+            if (!flip) { /* diagonal v00-v11 */
+                tri[0][0] = v00; tri[0][1] = v10; tri[0][2] = v11;
+                tri[1][0] = v00; tri[1][1] = v11; tri[1][2] = v01;
+            } else {     /* diagonal v10-v01 */
+                tri[0][0] = v00; tri[0][1] = v10; tri[0][2] = v01;
+                tri[1][0] = v10; tri[1][1] = v11; tri[1][2] = v01;
+            }
+            for (int k = 0; k < 2; ++k, ++e)
+                for (int a = 0; a < 3; ++a) s->elv[e * 3 + a] = tri[k][a];
+        } else {
+            for (int k = 0; k < 6; ++k, ++e) {
+                int p[3] = {ci[0], ci[1], ci[2]};
+                s->elv[e * 4 + 0] = p[0] + s->V * (p[1] + s->V * p[2]);
+                for (int m = 0; m < 3; ++m) {
+                    p[KUHN[k][m]] += 1;
+                    s->elv[e * 4 + m + 1] = p[0] + s->V * (p[1] + s->V * p[2]);
+                }
+            }
+        }
+    }
+
+    /* dof ids: vertex (i,j,k) -> dof-lattice point degree*(i,j,k); edge midpoint
+     * -> the mean of its endpoints' dof-lattice points. */
+    s->dx = (double *)malloc(sizeof(double) * s->ndof * dim);
+    for (int64_t i = 0; i < s->ndof * dim; ++i) s->dx[i] = NAN;
+    for (e = 0; e < s->nel; ++e) {
+        int lat[4][3];
+        for (int a = 0; a < s->nvert_el; ++a) {
+            int64_t t = s->elv[e * s->nvert_el + a];
+            for (int d = 0; d < 3; ++d) { lat[a][d] = 0; }
+            for (int d = 0; d < dim; ++d) { lat[a][d] = (int)(t % s->V) * degree; t /= s->V; }
+        }
+        for (int a = 0; a < s->nvert_el; ++a) {
+            int64_t id = 0, mul = 1;
+            for (int d = 0; d < dim; ++d) { id += lat[a][d] * mul; mul *= s->S; }
+            s->eld[e * s->nloc + a] = (int32_t)id;
+            const int32_t v = s->elv[e * s->nvert_el + a];
+            for (int d = 0; d < dim; ++d) s->dx[id * dim + d] = s->vx[(int64_t)v * dim + d];
+        }
+        if (degree == 2) {
+            const int ne = dim == 2 ? 3 : 6;
+            for (int m = 0; m < ne; ++m) {
+                const int a = dim == 2 ? EDGES2[m][0] : EDGES3[m][0];
+                const int b = dim == 2 ? EDGES2[m][1] : EDGES3[m][1];
+                int64_t id = 0, mul = 1;
+                for (int d = 0; d < dim; ++d) { id += ((lat[a][d] + lat[b][d]) / 2) * mul; mul *= s->S; }
+                s->eld[e * s->nloc + s->nvert_el + m] = (int32_t)id;
+                const int32_t va = s->elv[e * s->nvert_el + a], vb = s->elv[e * s->nvert_el + b];
+                for (int d = 0; d < dim; ++d)
+                    s->dx[id * dim + d] = (s->vx[(int64_t)va * dim + d] + s->vx[(int64_t)vb * dim + d]) * 0.5;
+            }
+        }
+    }
+
+    /* boundary: a dof-lattice coordinate equal to 0 or S-1.  Free and boundary
+     * dofs keep the order of the full numbering. */
+    s->free_of_full = (int32_t *)malloc(sizeof(int32_t) * s->ndof);
+    s->bnd_of_full = (int32_t *)malloc(sizeof(int32_t) * s->ndof);
+    s->nfree = s->nbnd = 0;
+    for (int64_t i = 0; i < s->ndof; ++i) {
+        int64_t t = i;
+        int onb = 0;
+        for (int d = 0; d < dim; ++d) {
+            int c = (int)(t % s->S); t /= s->S;
+            if (c == 0 || c == s->S - 1) onb = 1;
+        }
+        if (onb) { s->bnd_of_full[i] = (int32_t)s->nbnd++; s->free_of_full[i] = -1; }
+        else { s->free_of_full[i] = (int32_t)s->nfree++; s->bnd_of_full[i] = -1; }
+    }
+    s->full_of_free = (int32_t *)malloc(sizeof(int32_t) * (s->nfree ? s->nfree : 1));
+    s->full_of_bnd = (int32_t *)malloc(sizeof(int32_t) * (s->nbnd ? s->nbnd : 1));
+    for (int64_t i = 0; i < s->ndof; ++i) {
+        if (s->free_of_full[i] >= 0) s->full_of_free[s->free_of_full[i]] = (int32_t)i;
+        else s->full_of_bnd[s->bnd_of_full[i]] = (int32_t)i;
+    }
+    return s;
+}
+
+void orc_sizes(const orc_sys *s, int64_t out[9]) {
+    out[0] = s->nv; out[1] = s->ndof; out[2] = s->nel; out[3] = s->nloc;
+    out[4] = s->nfree; out[5] = s->nbnd; out[6] = s->nnz_full; out[7] = s->nnz_ii; out[8] = s->nnz_ib;
+}
+
+void orc_get_vertex_coords(const orc_sys *s, double *out) {
+    memcpy(out, s->vx, sizeof(double) * s->nv * s->dim);
+}
+void orc_get_dof_coords(const orc_sys *s, double *out) {
+    memcpy(out, s->dx, sizeof(double) * s->ndof * s->dim);
+}
+void orc_get_elements(const orc_sys *s, int32_t *out) {
+    memcpy(out, s->eld, sizeof(int32_t) * s->nel * s->nloc);
+}
+void orc_get_maps(const orc_sys *s, int32_t *fof, int32_t *bof, int32_t *foff, int32_t *fofb) {
+    if (fof) memcpy(fof, s->free_of_full, sizeof(int32_t) * s->ndof);
+    if (bof) memcpy(bof, s->bnd_of_full, sizeof(int32_t) * s->ndof);
+    if (foff) memcpy(foff, s->full_of_free, sizeof(int32_t) * s->nfree);
+    if (fofb) memcpy(fofb, s->full_of_bnd, sizeof(int32_t) * s->nbnd);
+}
+
+/* ------------------------------------------------------ element matrix -- */
+/* Barycentric gradients of a simplex with vertices P[0..d]: with J the matrix
+ * whose columns are P[a]-P[0] (a=1..d), lambda_a for a>=1 are the entries of
+ * J^{-1}(x-P[0]), so grad(lambda_a) is row a-1 of J^{-1}, and
+ * grad(lambda_0) = -sum_{a>=1} grad(lambda_a).  |T| = |det J| / d!. */
+static double simplex_gradients(int dim, const double P[4][3], double g[4][3]) {
+    double J[3][3] = {{0}};
+    for (int a = 1; a <= dim; ++a)
+        for (int r = 0; r < dim; ++r) J[r][a - 1] = P[a][r] - P[0][r];
+    double det, inv[3][3];
+    if (dim == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        inv[0][0] = J[1][1] / det;  inv[0][1] = -J[0][1] / det;
+        inv[1][0] = -J[1][0] / det; inv[1][1] = J[0][0] / det;
+    } else {
+        /* inverse = adjugate / det; adjugate = transpose of the cofactors */
+        double cof[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                const int r1 = (r + 1) % 3, r2 = (r + 2) % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                cof[r][c] = J[r1][c1] * J[r2][c2] - J[r1][c2] * J[r2][c1];
+            }
+        det = J[0][0] * cof[0][0] + J[0][1] * cof[0][1] + J[0][2] * cof[0][2];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) inv[r][c] = cof[c][r] / det;
+    }
+    for (int a = 1; a <= dim; ++a)
+        for (int c = 0; c < dim; ++c) g[a][c] = inv[a - 1][c];
+    for (int c = 0; c < dim; ++c) {
+        double t = 0.0;
+        for (int a = 1; a <= dim; ++a) t += g[a][c];
+        g[0][c] = -t;
+    }
+    return fabs(det) / (dim == 2 ? 2.0 : 6.0);
+}
+
+/* Gradient of local basis function i written as sum_{m,c} C[m][c] lambda_m grad(lambda_c)
+ * (homogeneous in lambda because sum_m lambda_m = 1):
+ *   P2 vertex a: phi = lambda_a (2 lambda_a - 1), grad = (4 lambda_a - 1) g_a
+ *                -> C[m][a] = 3 if m == a else -1;
+ *   P2 edge (a,b): phi = 4 lambda_a lambda_b, grad = 4 lambda_a g_b + 4 lambda_b g_a. */
+static void p2_grad_coeffs(int dim, int i, double C[4][4]) {
+    for (int m = 0; m < 4; ++m)
+        for (int c = 0; c < 4; ++c) C[m][c] = 0.0;
+    const int nv = dim + 1;
+    if (i < nv) {
+        for (int m = 0; m < nv; ++m) C[m][i] = (m == i) ? 3.0 : -1.0;
+    } else {
+        const int k = i - nv;
+        const int a = dim == 2 ? EDGES2[k][0] : EDGES3[k][0];
+        const int b = dim == 2 ? EDGES2[k][1] : EDGES3[k][1];
+        C[a][b] = 4.0;
+        C[b][a] = 4.0;
+    }
+}
+
+void orc_element_matrix(const orc_sys *s, int64_t e, double *out) {
+    const int dim = s->dim, nv = dim + 1, nloc = s->nloc;
+    double P[4][3] = {{0}}, g[4][3] = {{0}};
+    for (int a = 0; a < nv; ++a) {
+        const int32_t v = s->elv[e * nv + a];
+        for (int d = 0; d < dim; ++d) P[a][d] = s->vx[(int64_t)v * dim + d];
+    }
+    const double vol = simplex_gradients(dim, P, g);
+    double G[4][4];
+    for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b) {
+            double t = 0.0;
+            for (int d = 0; d < dim; ++d) t += g[a][d] * g[b][d];
+            G[a][b] = t;
+        }
+    if (s->degree == 1) {
+        /* K_ab = |T| grad(lambda_a).grad(lambda_b) */
+        for (int a = 0; a < nv; ++a)
+            for (int b = 0; b < nv; ++b) out[a * nloc + b] = vol * G[a][b];
+        return;
+    }
+    /* int_T lambda_m lambda_n = |T| d! (1 + delta_mn) / (d+2)! */
+    const double fact = dim == 2 ? 2.0 / 24.0 : 6.0 / 120.0;
+    double M[4][4];
+    for (int m = 0; m < nv; ++m)
+        for (int n = 0; n < nv; ++n) M[m][n] = vol * fact * (m == n ? 2.0 : 1.0);
+    double Ci[4][4], Cj[4][4];
+    for (int i = 0; i < nloc; ++i) {
+        p2_grad_coeffs(dim, i, Ci);
+        for (int j = i; j < nloc; ++j) {
+            p2_grad_coeffs(dim, j, Cj);
+            /* K_ij = sum_{m,c,n,e} Ci[m][c] Cj[n][e] (g_c.g_e) int lambda_m lambda_n */
+            double t = 0.0;
+            for (int m = 0; m < nv; ++m)
+                for (int c = 0; c < nv; ++c) {
+                    if (Ci[m][c] == 0.0) continue;
+                    for (int n = 0; n < nv; ++n)
+                        for (int ee = 0; ee < nv; ++ee) {
+                            if (Cj[n][ee] == 0.0) continue;
+                            t += Ci[m][c] * Cj[n][ee] * G[c][ee] * M[m][n];
+                        }
+                }
+            out[i * nloc + j] = t;
+            out[j * nloc + i] = t;
+        }
+    }
+}
+
+/* ------------------------------------------------------------ assembly -- */
+typedef struct { int32_t col; double val; } trip;
+
+/* stable insertion sort by column (keeps element order among duplicates) */
+static void sort_row(trip *t, int64_t m) {
+    for (int64_t i = 1; i < m; ++i) {
+        trip x = t[i];
+        int64_t j = i - 1;
+        while (j >= 0 && t[j].col > x.col) { t[j + 1] = t[j]; --j; }
+        t[j + 1] = x;
+    }
+}
+
+int orc_assemble(orc_sys *s, const uint8_t *row_mask) {
+    free_assembly(s);
+    const int nloc = s->nloc;
+    /* pass 1: triplet count per selected row */
+    int64_t *cnt = (int64_t *)calloc((size_t)s->ndof + 1, sizeof(int64_t));
+    for (int64_t e = 0; e < s->nel; ++e)
+        for (int a = 0; a < nloc; ++a) {
+            const int32_t i = s->eld[e * nloc + a];
+            if (!row_mask || row_mask[i]) cnt[i + 1] += nloc;
+        }
+    for (int64_t i = 0; i < s->ndof; ++i) cnt[i + 1] += cnt[i];
+    const int64_t ntrip = cnt[s->ndof];
+    trip *T = (trip *)malloc(sizeof(trip) * (ntrip ? ntrip : 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (s->ndof ? s->ndof : 1));
+    memcpy(pos, cnt, sizeof(int64_t) * s->ndof);
+    /* pass 2: scatter element matrices in element order */
+    double Ke[100];
+    for (int64_t e = 0; e < s->nel; ++e) {
+        int any = !row_mask;
+        for (int a = 0; a < nloc && !any; ++a) any = row_mask[s->eld[e * nloc + a]] != 0;
+        if (!any) continue;
+        orc_element_matrix(s, e, Ke);
+        for (int a = 0; a < nloc; ++a) {
+            const int32_t i = s->eld[e * nloc + a];
+            if (row_mask && !row_mask[i]) continue;
+            for (int b = 0; b < nloc; ++b) {
+                T[pos[i]].col = s->eld[e * nloc + b];
+                T[pos[i]].val = Ke[a * nloc + b];
+                pos[i]++;
+            }
+        }
+    }
+    free(pos);
+    /* pass 3: per row, sort by column and sum duplicates in element order */
+    s->rp_full = (int64_t *)malloc(sizeof(int64_t) * (s->ndof + 1));
+    s->rp_full[0] = 0;
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < s->ndof; ++i) {
+        trip *t = T + cnt[i];
+        const int64_t m = cnt[i + 1] - cnt[i];
+        sort_row(t, m);
+        int64_t w = 0;
+        for (int64_t k = 0; k < m; ++k) {
+            if (w > 0 && t[w - 1].col == t[k].col) t[w - 1].val += t[k].val;
+            else t[w++] = t[k];
+        }
+        nnz += w;
+        s->rp_full[i + 1] = nnz;
+    }
+    s->nnz_full = nnz;
+    s->ci_full = (int32_t *)malloc(sizeof(int32_t) * (nnz ? nnz : 1));
+    s->v_full = (double *)malloc(sizeof(double) * (nnz ? nnz : 1));
+    for (int64_t i = 0; i < s->ndof; ++i) {
+        const trip *t = T + cnt[i];
+        const int64_t w = s->rp_full[i + 1] - s->rp_full[i];
+        for (int64_t k = 0; k < w; ++k) {
+            s->ci_full[s->rp_full[i] + k] = t[k].col;
+            s->v_full[s->rp_full[i] + k] = t[k].val;
+        }
+    }
+    free(T);
+    free(cnt);
+
+    /* split: free rows; free columns -> K_II (free numbering), boundary
+     * columns -> K_IB (boundary numbering).  Both keep ascending columns. */
+    s->rp_ii = (int64_t *)malloc(sizeof(int64_t) * (s->nfree + 1));
+    s->rp_ib = (int64_t *)malloc(sizeof(int64_t) * (s->nfree + 1));
+    s->rp_ii[0] = s->rp_ib[0] = 0;
+    for (int64_t f = 0; f < s->nfree; ++f) {
+        const int32_t i = s->full_of_free[f];
+        int64_t a = 0, b = 0;
+        for (int64_t k = s->rp_full[i]; k < s->rp_full[i + 1]; ++k) {
+            if (s->free_of_full[s->ci_full[k]] >= 0) ++a; else ++b;
+        }
+        s->rp_ii[f + 1] = s->rp_ii[f] + a;
+        s->rp_ib[f + 1] = s->rp_ib[f] + b;
+    }
+    s->nnz_ii = s->rp_ii[s->nfree];
+    s->nnz_ib = s->rp_ib[s->nfree];
+    s->ci_ii = (int32_t *)malloc(sizeof(int32_t) * (s->nnz_ii ? s->nnz_ii : 1));
+    s->v_ii = (double *)malloc(sizeof(double) * (s->nnz_ii ? s->nnz_ii : 1));
+    s->ci_ib = (int32_t *)malloc(sizeof(int32_t) * (s->nnz_ib ? s->nnz_ib : 1));
+    s->v_ib = (double *)malloc(sizeof(double) * (s->nnz_ib ? s->nnz_ib : 1));
+    for (int64_t f = 0; f < s->nfree; ++f) {
+        const int32_t i = s->full_of_free[f];
+        int64_t a = s->rp_ii[f], b = s->rp_ib[f];
+        for (int64_t k = s->rp_full[i]; k < s->rp_full[i + 1]; ++k) {
+            const int32_t j = s->ci_full[k];
+            if (s->free_of_full[j] >= 0) { s->ci_ii[a] = s->free_of_full[j]; s->v_ii[a++] = s->v_full[k]; }
+            else { s->ci_ib[b] = s->bnd_of_full[j]; s->v_ib[b++] = s->v_full[k]; }
+        }
+    }
+    return 0;
+}
+
+void orc_get_full(const orc_sys *s, int64_t *rp, int32_t *ci, double *v) {
+    if (rp) memcpy(rp, s->rp_full, sizeof(int64_t) * (s->ndof + 1));
+    if (ci) memcpy(ci, s->ci_full, sizeof(int32_t) * s->nnz_full);
+    if (v) memcpy(v, s->v_full, sizeof(double) * s->nnz_full);
+}
+void orc_get_ii(const orc_sys *s, int64_t *rp, int32_t *ci, double *v) {
+    if (rp) memcpy(rp, s->rp_ii, sizeof(int64_t) * (s->nfree + 1));
+    if (ci) memcpy(ci, s->ci_ii, sizeof(int32_t) * s->nnz_ii);
+    if (v) memcpy(v, s->v_ii, sizeof(double) * s->nnz_ii);
+}
+void orc_get_ib(const orc_sys *s, int64_t *rp, int32_t *ci, double *v) {
+    if (rp) memcpy(rp, s->rp_ib, sizeof(int64_t) * (s->nfree + 1));
+    if (ci) memcpy(ci, s->ci_ib, sizeof(int32_t) * s->nnz_ib);
+    if (v) memcpy(v, s->v_ib, sizeof(double) * s->nnz_ib);
+}
+
+/* ------------------------------------------------------- Dirichlet data -- */
+static int ncoef(int gid) { return gid == 3 ? 4 : (gid == 4 ? 10 : 0); }
+
+static double gfun(int gid, const double *c, const double *p, int dim) {
+    const double x = p[0], y = p[1], z = dim == 3 ? p[2] : 0.0;
+    const double PI = 3.14159265358979323846;
+    switch (gid) {
+    case 0: return sin(PI * x) * sinh(PI * y) / sinh(PI);
+    case 1: return x * x - y * y;
+    case 2: return x * x + y * y - 2.0 * z * z;
+    case 3: return c[0] + c[1] * x + c[2] * y + c[3] * z;
+    case 4: {
+        /* Re/Im of (x+iy)^k, k=0..4, written out as real polynomials */
+        const double re[5] = {1.0, x, x * x - y * y, x * x * x - 3.0 * x * y * y,
+                              x * x * x * x - 6.0 * x * x * y * y + y * y * y * y};
+        const double im[5] = {0.0, y, 2.0 * x * y, 3.0 * x * x * y - y * y * y,
+                              4.0 * x * x * x * y - 4.0 * x * y * y * y};
+        double t = 0.0;
+        for (int k = 0; k < 5; ++k) t += c[2 * k] * re[k] + c[2 * k + 1] * im[k];
+        return t;
+    }
+    default: return NAN;
+    }
+}
+
+int orc_eval_g(const orc_sys *s, int gid, const double *coef, int k, int which, double *out) {
+    if (gid < 0 || gid > 4 || k < 1) return 1;
+    const int nc = ncoef(gid);
+    const int64_t rows = which == 0 ? s->nbnd : s->nfree;
+    for (int64_t r = 0; r < rows; ++r) {
+        const int32_t i = which == 0 ? s->full_of_bnd[r] : s->full_of_free[r];
+        for (int c = 0; c < k; ++c)
+            out[r * k + c] = gfun(gid, coef ? coef + (int64_t)c * nc : NULL, s->dx + (int64_t)i * s->dim, s->dim);
+    }
+    return 0;
+}
+
+void orc_lift(const orc_sys *s, const double *gB, int k, double *b) {
+    for (int64_t f = 0; f < s->nfree; ++f)
+        for (int c = 0; c < k; ++c) {
+            double t = 0.0;
+            for (int64_t q = s->rp_ib[f]; q < s->rp_ib[f + 1]; ++q)
+                t += s->v_ib[q] * gB[(int64_t)s->ci_ib[q] * k + c];
+            b[f * k + c] = -t;
+        }
+}
+
+/* -------------------------------------------------------------- solvers -- */
+void orc_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+              const double *x, double *y) {
+    for (int64_t i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) t += v[k] * x[ci[k]];
+        y[i] = t;
+    }
+}
+
+static double dot(int64_t n, const double *a, const double *b) {
+    double t = 0.0;
+    for (int64_t i = 0; i < n; ++i) t += a[i] * b[i];
+    return t;
+}
+
+/* Preconditioned CG (Hestenes-Stiefel) with M = diag(A):
+ *   r = b - A x, z = M^{-1} r, p = z, rho = r.z
+ *   repeat: q = A p; alpha = rho / p.q; x += alpha p; r -= alpha q;
+ *           stop if ||r|| / ||b|| <= tol (Eq. 2);
+ *           z = M^{-1} r; rho' = r.z; beta = rho'/rho; p = z + beta p.
+ * At a stop on the recursive residual the true residual b - A x is formed;
+ * if it is above tol, r is replaced by it and the recurrence restarts. */
+int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+            const double *b, double *x, double tol, int64_t maxit,
+            int64_t *iters, double *relres) {
+    *iters = 0;
+    const double bn = sqrt(dot(n, b, b));
+    if (bn == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        *relres = 0.0;
+        return 0;
+    }
+    double *dinv = (double *)malloc(sizeof(double) * n);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *z = (double *)malloc(sizeof(double) * n);
+    double *p = (double *)malloc(sizeof(double) * n);
+    double *q = (double *)malloc(sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) if (ci[k] == i) d = v[k];
+        dinv[i] = 1.0 / d;
+    }
+    int status = 1;
+    int64_t it = 0;
+    int restarts = 0;
+    orc_spmv(n, rp, ci, v, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    double rel = sqrt(dot(n, r, r)) / bn;
+    while (status == 1) {
+        if (rel <= tol) { status = 0; break; }
+        for (int64_t i = 0; i < n; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
+        double rho = dot(n, r, z);
+        int restart = 0;
+        while (it < maxit) {
+            orc_spmv(n, rp, ci, v, p, q);
+            const double pq = dot(n, p, q);
+            if (!(pq > 0.0) || !isfinite(pq)) { status = 2; break; }
+            const double alpha = rho / pq;
+            for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+            ++it;
+            rel = sqrt(dot(n, r, r)) / bn;
+            if (rel <= tol) {
+                orc_spmv(n, rp, ci, v, x, q);
+                for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+                const double tr = sqrt(dot(n, q, q)) / bn;
+                if (tr <= tol) { rel = tr; status = 0; break; }
+                for (int64_t i = 0; i < n; ++i) r[i] = q[i];
+                rel = tr;
+                restart = 1;
+                break;
+            }
+            for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            const double rho1 = dot(n, r, z);
+            const double beta = rho1 / rho;
+            rho = rho1;
+            for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        }
+        if (status != 1) break;
+        if (!restart || it >= maxit || ++restarts > 50) break;
+    }
+    *iters = it;
+    *relres = rel;
+    free(dinv); free(r); free(z); free(p); free(q);
+    return status;
+}
+
+int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                       const double *b, double *x) {
+    double *L = (double *)calloc((size_t)(n * n), sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) L[i * n + ci[k]] = v[k];
+    /* A = L L^T, lower triangle overwritten (textbook column-by-column form) */
+    for (int64_t j = 0; j < n; ++j) {
+        double d = L[j * n + j];
+        for (int64_t k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > 0.0)) { free(L); return 1; }
+        d = sqrt(d);
+        L[j * n + j] = d;
+        for (int64_t i = j + 1; i < n; ++i) {
+            double t = L[i * n + j];
+            for (int64_t k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / d;
+        }
+    }
+    /* L y = b, then L^T x = y */
+    for (int64_t i = 0; i < n; ++i) {
+        double t = b[i];
+        for (int64_t k = 0; k < i; ++k) t -= L[i * n + k] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double t = x[i];
+        for (int64_t k = i + 1; k < n; ++k) t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+    free(L);
+    return 0;
+}
+
+/* ----------------------------------------------------------- SELL-C-sigma -- */
+/* Rows are cut into windows of sigma consecutive rows; inside a window they are
+ * ordered by descending row length, ties kept in original order (stable).  The
+ * new order is cut into chunks of C rows; a chunk's width is its longest row. */
+static void sell_perm(int64_t n, const int64_t *rp, int sigma, int32_t *perm) {
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    if (sigma <= 1) return;
+    for (int64_t w0 = 0; w0 < n; w0 += sigma) {
+        const int64_t w1 = w0 + sigma < n ? w0 + sigma : n;
+        /* stable insertion sort of perm[w0..w1) by descending length */
+        for (int64_t i = w0 + 1; i < w1; ++i) {
+            const int32_t x = perm[i];
+            const int64_t lx = rp[x + 1] - rp[x];
+            int64_t j = i - 1;
+            while (j >= w0 && (rp[perm[j] + 1] - rp[perm[j]]) < lx) { perm[j + 1] = perm[j]; --j; }
+            perm[j + 1] = x;
+        }
+    }
+}
+
+void orc_sell_size(int64_t n, const int64_t *rp, int C, int sigma, int64_t *nchunks, int64_t *padded) {
+    int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (n ? n : 1));
+    sell_perm(n, rp, sigma, perm);
+    const int64_t nc = (n + C - 1) / C;
+    int64_t tot = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t w = 0;
+        for (int64_t r = c * C; r < (c + 1) * C && r < n; ++r) {
+            const int64_t l = rp[perm[r] + 1] - rp[perm[r]];
+            if (l > w) w = l;
+        }
+        tot += w * C;
+    }
+    *nchunks = nc;
+    *padded = tot;
+    free(perm);
+}
+
+void orc_sell_fill(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                   int C, int sigma, int32_t *perm, int64_t *chunk_ptr,
+                   int32_t *chunk_w, int32_t *row_len, int32_t *col, double *val) {
+    sell_perm(n, rp, sigma, perm);
+    int32_t *iperm = (int32_t *)malloc(sizeof(int32_t) * (n ? n : 1));
+    for (int64_t r = 0; r < n; ++r) iperm[perm[r]] = (int32_t)r;
+    const int64_t nc = (n + C - 1) / C;
+    chunk_ptr[0] = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        int64_t w = 0;
+        for (int64_t r = c * C; r < (c + 1) * C && r < n; ++r) {
+            const int64_t l = rp[perm[r] + 1] - rp[perm[r]];
+            if (l > w) w = l;
+        }
+        chunk_w[c] = (int32_t)w;
+        chunk_ptr[c + 1] = chunk_ptr[c] + w * C;
+        for (int64_t j = 0; j < w; ++j)
+            for (int64_t t = 0; t < C; ++t) {
+                const int64_t r = c * C + t;
+                const int64_t slot = chunk_ptr[c] + j * C + t;
+                if (r < n) {
+                    const int32_t o = perm[r];
+                    const int64_t l = rp[o + 1] - rp[o];
+                    if (j < l) { col[slot] = iperm[ci[rp[o] + j]]; if (val) val[slot] = v[rp[o] + j]; }
+                    else { col[slot] = (int32_t)r; if (val) val[slot] = 0.0; }
+                } else {
+                    col[slot] = 0;
+                    if (val) val[slot] = 0.0;
+                }
+            }
+    }
+    for (int64_t r = 0; r < n; ++r) row_len[r] = (int32_t)(rp[perm[r] + 1] - rp[perm[r]]);
+    free(iperm);
+}
