@@ -1,0 +1,241 @@
+/*
+ * gbpcg.h -- C ABI of the GB300 (sm_103a) FEM-Laplace Jacobi-PCG library.
+ *
+ * The library solves the sparse SPD systems that come from discretising
+ * Laplace's equation with Dirichlet data (paper Sec. 2.2) by P1/P2 finite
+ * elements on lattice meshes, with one or many right-hand sides (Eq. MRH,
+ * Sec. 4.3), by Jacobi-preconditioned conjugate gradients (the preconditioned
+ * Krylov solve of Sec. 2.1) stopped by the relative residual of Eq. (2).
+ * Every step runs in CUDA kernels of this library; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *    owns every buffer it passes; the library owns the opaque handles it
+ *    returns and everything reachable from them, and allocates through the
+ *    caller's gb_allocator (NULL = cudaMalloc/cudaFree).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; entry points that must return sizes or statistics
+ *    synchronise that stream before returning (stated per function).
+ *  - Return value: GB_OK (0) or a negative GB_E* code; gbpcg_last_error()
+ *    returns a thread-local message for the last failure.  Arguments are
+ *    validated before any work is enqueued.
+ *  - Vectors passed to the solvers are in the free-dof order of the system
+ *    (increasing lexicographic dof-lattice index, x fastest); multi-RHS blocks
+ *    are row-major n x k.  The library's internal row permutation never shows.
+ *  - Index type is int32: a system needs n, nnz and padded nnz below 2^31.
+ */
+#ifndef GBPCG_H
+#define GBPCG_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GB_OK = 0,
+    GB_EINVAL = -1,          /* bad argument */
+    GB_ENOMEM = -2,          /* allocator returned NULL */
+    GB_ECUDA = -3,           /* a CUDA runtime call failed */
+    GB_NOT_CONVERGED = -4,   /* max_iter reached; x and stats are still written */
+    GB_BREAKDOWN = -5,       /* p.Ap <= 0 or non-finite: matrix not SPD or bad data */
+    GB_TIMEOUT = -6,         /* a device-side bounded wait ran out */
+    GB_TOO_LARGE = -7,       /* request exceeds a size limit or the memory budget */
+    GB_PENDING = 1           /* serve_poll: request not finished yet */
+};
+
+/* Thread-local message of the last failing call on this thread. */
+const char *gbpcg_last_error(void);
+/* Library version string. */
+const char *gbpcg_version(void);
+/* Kernels this process has launched through the library so far (launches
+ * replayed by a CUDA graph's loop included). */
+int64_t gbpcg_kernel_launches(void);
+
+/* Device memory supplier.  alloc(ctx, bytes, stream) returns a device pointer
+ * aligned to at least 256 bytes, or NULL; free(ctx, ptr, stream) releases it.
+ * Both are called from the calling thread only, never from a kernel. */
+typedef struct gb_allocator {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes, void *stream);
+    void (*free)(void *ctx, void *ptr, void *stream);
+} gb_allocator;
+
+/* ------------------------------------------------------------ assembly --
+ * Mesh of the unit square (dim 2) or cube (dim 3) with `cells` cells per side
+ * (Sec. 2.2 case study).  2D: each cell is cut into two triangles by its
+ * SW-NE diagonal, or by a per-cell random diagonal (diag_mode 1: the NW-SE one
+ * when the cell's draw is below 1/2); with jitter=1 every interior vertex moves
+ * by (2u-1)h/4 per coordinate.  3D: Kuhn split of each cube into six
+ * tetrahedra along its main diagonal (jitter must be 0).  The draws u come
+ * from the counter-based SplitMix64 generator: output i of stream s of run
+ * `seed` is mix64(key + (i+1)*0x9E3779B97F4A7C15), key = seed*2^40 xor s*2^32,
+ * u = (output >> 11) * 2^-53; stream 0/1 jitter x/y (i = vertex id), stream 2
+ * the diagonal (i = cell id).  degree 1 (P1) or 2 (P2, Sec. 4.2 / Table 7):
+ * dofs are the points of the lattice with degree*cells+1 points per side;
+ * boundary dofs are those with a coordinate 0 or degree*cells. */
+typedef struct gb_fem_spec {
+    int32_t dim;        /* 2 or 3 */
+    int32_t degree;     /* 1 or 2 */
+    int32_t cells;      /* cells per side, >= 2 */
+    int32_t jitter;     /* 0 or 1 (2D only) */
+    int32_t diag_mode;  /* 0 fixed SW-NE, 1 random per cell (2D only) */
+    int32_t reserved;   /* must be 0 */
+    uint64_t seed;
+} gb_fem_spec;
+
+typedef struct gb_fem_system gb_fem_system;
+
+/* Read-only views of an assembled system (device pointers owned by it). */
+typedef struct gb_fem_info {
+    int64_t n_dof, n_free, n_bnd;
+    int64_t nnz;        /* stored entries of K_II (structural: never value-dropped) */
+    int64_t nnz_ib;     /* stored entries of K_IB */
+    int32_t dim, degree, cells, side;  /* side = dof-lattice points per side */
+    int32_t max_row;    /* longest row of K_II */
+    int32_t reserved;
+    const int32_t *d_rowptr;     /* K_II CSR, n_free+1, columns ascending */
+    const int32_t *d_col;
+    const double *d_val;
+    const int32_t *d_rowptr_ib;  /* K_IB CSR (columns = boundary ids) */
+    const int32_t *d_col_ib;
+    const double *d_val_ib;
+    const double *d_diag;        /* diag(K_II), n_free */
+} gb_fem_info;
+
+/* Builds the mesh, numbers the dofs, assembles the stiffness
+ * K_ij = sum_T int_T grad(phi_i).grad(phi_j) and splits it into the free block
+ * K_II and the coupling K_IB (Dirichlet elimination, Sec. 2.2).  Each row is
+ * gathered over its incident elements in a fixed order, so K_II is
+ * bit-exactly symmetric and the result is deterministic.  Synchronises
+ * `stream` once (to size the column arrays). */
+int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, void *stream,
+                 gb_fem_system **out);
+int fem_system_info(const gb_fem_system *sys, gb_fem_info *out);
+/* Free-dof <-> full-dof maps (device int32 arrays of n_free / n_bnd / n_dof). */
+int fem_dof_maps(const gb_fem_system *sys, int32_t *d_full_of_free, int32_t *d_full_of_bnd,
+                 int32_t *d_free_of_full, void *stream);
+/* Coordinates of the boundary (which=0, n_bnd rows) or free (which=1, n_free
+ * rows) dofs, row-major rows x dim.  P2 edge dofs sit at edge midpoints. */
+int fem_boundary_coords(const gb_fem_system *sys, int which, double *d_xyz, void *stream);
+/* Dirichlet data g at the boundary (which=0) or free (which=1) dofs for k
+ * columns, row-major rows x k.  gid: 0 sin(pi x)sinh(pi y)/sinh(pi);
+ * 1 x^2-y^2; 2 x^2+y^2-2z^2; 3 c0+c1 x+c2 y+c3 z (4 coefficients per column);
+ * 4 sum_{m=0..4} a_m Re(x+iy)^m + b_m Im(x+iy)^m (10 coefficients per column,
+ * ordered a_0,b_0,a_1,b_1,...).  h_coef: host array, k*ncoef values (NULL when
+ * ncoef is 0).  Synchronous in h_coef only (copied before return). */
+int fem_dirichlet(const gb_fem_system *sys, int gid, const double *h_coef, int k, int which,
+                  double *d_out, void *stream);
+/* b = -K_IB g_B for k columns (row-major: d_gB n_bnd x k, d_b n_free x k). */
+int fem_lift_rhs(const gb_fem_system *sys, const double *d_gB, int k, double *d_b, void *stream);
+void fem_system_destroy(gb_fem_system *sys);
+
+/* ---------------------------------------------------------- SELL-C-sigma --
+ * Sliced ELLPACK with sorting window sigma: rows are ordered by descending
+ * length inside windows of sigma consecutive rows (stable), cut into chunks of
+ * C rows, each chunk stored column-major and padded to its longest row
+ * (padding: the row's own index, value 0).  The permutation is applied
+ * symmetrically (rows and columns).  val_types: bit 0 fp64, bit 1 fp32,
+ * bit 2 bf16 value copies (fp64 is always kept; fp32/bf16 serve the mixed-
+ * precision inner solve).  C in {32, 64, 128}; sigma >= 1. */
+enum { GB_VAL_F64 = 1, GB_VAL_F32 = 2, GB_VAL_BF16 = 4 };
+
+typedef struct gb_sell gb_sell;
+
+typedef struct gb_sell_info {
+    int64_t n, nnz, padded, nchunks;
+    int32_t C, sigma, max_row, reserved;
+    const int32_t *d_perm;       /* perm[new] = old */
+    const int64_t *d_chunk_ptr;  /* nchunks+1 */
+    const int32_t *d_chunk_w;    /* nchunks */
+    const int32_t *d_row_len;    /* n, new order */
+    const int32_t *d_col;        /* padded, new numbering */
+    const double *d_val;         /* padded fp64 */
+    const double *d_dinv;        /* 1/diag, new order */
+} gb_sell_info;
+
+/* From an assembled system's K_II.  Asynchronous except for one sync to read
+ * the padded size. */
+int csr_to_sell(const gb_fem_system *sys, int C, int sigma, int val_types,
+                const gb_allocator *alloc, void *stream, gb_sell **out);
+/* From any CSR matrix with a non-zero diagonal (device arrays; int32 rowptr). */
+int csr_to_sell_raw(int64_t n, const int32_t *d_rowptr, const int32_t *d_col, const double *d_val,
+                    int C, int sigma, int val_types, const gb_allocator *alloc, void *stream,
+                    gb_sell **out);
+int sell_info(const gb_sell *A, gb_sell_info *out);
+/* y = A x through the SELL storage (x, y in the original order). */
+int sell_spmv(const gb_sell *A, const double *d_x, double *d_y, void *stream);
+void sell_destroy(gb_sell *A);
+
+/* ------------------------------------------------------------------ PCG --
+ * Jacobi-PCG: r = b - A x0, z = D^{-1} r, p = z; iterate q = A p,
+ * alpha = r.z / p.q, x += alpha p, r -= alpha q, z = D^{-1} r, beta = r.z'/r.z,
+ * p = z + beta p; stop when ||r||/||b|| <= tol (Eq. 2), then confirm on the
+ * true residual b - A x in fp64 (restart from it if it is above tol).
+ * precision GB_F64: everything in fp64.  GB_F32_IR / GB_BF16_IR: iterative
+ * refinement -- fp64 outer residual b - A x, convergence test and update
+ * x += d; the correction d solves A d = r approximately by an inner PCG with
+ * fp32 vectors, fp32 accumulation and fp32 (or bf16-stored) matrix values to
+ * relative residual inner_tol.  If the refinement stalls (two outer steps
+ * without a 10% residual reduction) or runs out of outer steps above tol, the
+ * solve continues with fp64 PCG from the current x on the device, and
+ * stats.fallback_iterations counts those iterations. */
+enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2 };
+
+typedef struct PcgOptions {
+    double tol;            /* Eq. (2) threshold, e.g. 1e-10 */
+    int64_t max_iter;      /* total (inner) iterations cap; 0 = 20 n + 100 */
+    int32_t precision;     /* GB_F64 | GB_F32_IR | GB_BF16_IR */
+    int32_t max_outer;     /* refinement steps cap (IR only); 0 = 30 */
+    double inner_tol;      /* inner relative residual (IR only); 0 = 1e-4 */
+    int32_t check_every;   /* iterations per host convergence poll; 0 = auto */
+    int32_t use_graph;     /* 1 = replay captured CUDA graphs (default), 0 = direct launches */
+    int32_t x0_zero;       /* 1 = ignore d_x on entry and start from 0 */
+    int32_t reserved;
+} PcgOptions;
+
+typedef struct PcgStats {
+    int64_t iterations;    /* CG iterations (inner ones for IR) */
+    int64_t restarts;      /* true-residual restarts (F64) */
+    int32_t outer;         /* refinement steps (IR) */
+    int32_t status;        /* GB_OK / GB_NOT_CONVERGED / GB_BREAKDOWN */
+    double relres;         /* final true relative residual ||b - A x|| / ||b|| (fp64) */
+    double bnorm;          /* ||b||_2 */
+    double solve_ms;       /* device time of the solve (events on `stream`) */
+    int64_t kernel_launches;  /* kernels this solve launched */
+    double bytes_moved;    /* algorithmic bytes of the solve (matrix + vector streams) */
+    int64_t fallback_iterations;  /* IR only: fp64 PCG iterations run after the
+                                     refinement stalled above tol (0 if none) */
+} PcgStats;
+
+/* Solves A x = b for one right-hand side.  d_b, d_x: n doubles (x in: x0).
+ * Synchronises `stream` (convergence polling and statistics). */
+int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
+              void *stream, PcgStats *stats);
+
+/* Solves nsys systems, system s with k[s] right-hand sides (row-major
+ * n_s x k_s blocks d_B[s], d_X[s]).  Systems with k > 1 run blocked multi-RHS
+ * PCG: one SpMM pass per iteration serves all columns, each column keeps its
+ * own alpha, beta and convergence mask.  All systems advance in the same
+ * launches.  Synchronises `stream`; stats[s] per system (iterations = max
+ * over its columns). */
+int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
+                      double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
+                      PcgStats *stats);
+
+/* Measurement entry point (no counterpart in the paper): runs `iters` fp64
+ * (precision GB_F64) or fp32-inner (GB_F32_IR / GB_BF16_IR) CG iterations on
+ * A with right-hand side d_b from x = 0, as direct launches on `stream`, with
+ * a CUDA event pair around every launch, and writes the mean duration in
+ * milliseconds of each of the iteration's three kernels to h_ms[0] (SpMV +
+ * p.Ap), h_ms[1] (x, r update + r.z, r.r) and h_ms[2] (p update).  The
+ * iterations run even past convergence (the scalars are reset each time), so
+ * every timed launch does a full pass.  Synchronises `stream`. */
+int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters, void *stream,
+                     double *h_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

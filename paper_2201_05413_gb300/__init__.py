@@ -1,0 +1,14 @@
+"""GB300-native (sm_103a) Jacobi-PCG solver for FEM discretisations of the
+Laplace equation: device assembly, SELL-C-sigma SpMV/SpMM, fused PCG kernels,
+mixed-precision iterative refinement, batched and served solves.
+
+The compute path is the CUDA library ``libgbpcg.so`` (C ABI in
+``include/gbpcg.h``); this package only marshals arguments to it.
+"""
+from . import gbpcg
+from .api import FemSystem, Sell, pcg_solve_batched
+from .gbpcg import (GB_BF16_IR, GB_F32_IR, GB_F64, GB_VAL_BF16, GB_VAL_F32, GB_VAL_F64, GbError,
+                    load)
+
+__all__ = ["FemSystem", "Sell", "pcg_solve_batched", "GbError", "load", "gbpcg", "GB_F64",
+           "GB_F32_IR", "GB_BF16_IR", "GB_VAL_F64", "GB_VAL_F32", "GB_VAL_BF16"]

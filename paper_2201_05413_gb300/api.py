@@ -1,0 +1,211 @@
+"""Python objects over the C ABI: FemSystem (fem_assemble ...), Sell
+(csr_to_sell ...), pcg_solve and pcg_solve_batched.  Marshalling only:
+arguments become pointers and sizes, results come back as torch tensors that
+share or copy device memory.  Nothing here computes the method."""
+from __future__ import annotations
+
+import ctypes as C
+import sys
+
+import torch
+
+from . import gbpcg as G
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory (``__cuda_array_interface__``)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3,
+                                         "strides": None}
+
+
+def _view(ptr, shape, dtype):
+    typestr = {torch.int32: "<i4", torch.int64: "<i8", torch.float64: "<f8",
+               torch.float32: "<f4"}[dtype]
+    if int(ptr or 0) == 0 or any(s == 0 for s in shape):
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+def _opts(tol=1e-10, max_iter=0, precision=G.GB_F64, max_outer=0, inner_tol=0.0, check_every=0,
+          use_graph=1, x0_zero=1):
+    return G.PcgOptions(tol, max_iter, precision, max_outer, inner_tol, check_every, use_graph,
+                        x0_zero, 0)
+
+
+class FemSystem:
+    """An assembled FEM-Laplace system: fem_assemble + fem_system_info."""
+
+    def __init__(self, dim, degree, cells, jitter=0, diag_mode=0, seed=0, stream=None,
+                 use_torch_allocator=True):
+        self.spec = G.gb_fem_spec(dim, degree, cells, jitter, diag_mode, 0, seed)
+        self._stream = stream
+        h = C.c_void_p()
+        alloc = G.torch_allocator() if use_torch_allocator else None
+        G.check(G.lib().fem_assemble(C.byref(self.spec), alloc, G.stream_ptr(stream), C.byref(h)),
+                "fem_assemble")
+        self.handle = h
+        info = G.gb_fem_info()
+        G.check(G.lib().fem_system_info(h, C.byref(info)), "fem_system_info")
+        self.info = info
+        self.n_free, self.n_bnd, self.n_dof = info.n_free, info.n_bnd, info.n_dof
+        self.nnz, self.nnz_ib, self.max_row = info.nnz, info.nnz_ib, info.max_row
+        self.dim, self.degree = dim, degree
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and G._lib is not None and not sys.is_finalizing():
+            torch.cuda.synchronize()
+            G._lib.fem_system_destroy(h)
+            self.handle = None
+
+    # device views (copied, so they outlive the system)
+    def csr(self):
+        i = self.info
+        return (_view(i.d_rowptr, (self.n_free + 1,), torch.int32).clone(),
+                _view(i.d_col, (self.nnz,), torch.int32).clone(),
+                _view(i.d_val, (self.nnz,), torch.float64).clone())
+
+    def csr_ib(self):
+        i = self.info
+        return (_view(i.d_rowptr_ib, (self.n_free + 1,), torch.int32).clone(),
+                _view(i.d_col_ib, (self.nnz_ib,), torch.int32).clone(),
+                _view(i.d_val_ib, (self.nnz_ib,), torch.float64).clone())
+
+    def diag(self):
+        return _view(self.info.d_diag, (self.n_free,), torch.float64).clone()
+
+    def dof_maps(self):
+        fof = torch.empty(self.n_free, dtype=torch.int32, device="cuda")
+        fob = torch.empty(self.n_bnd, dtype=torch.int32, device="cuda")
+        ff = torch.empty(self.n_dof, dtype=torch.int32, device="cuda")
+        G.check(G.lib().fem_dof_maps(self.handle, G.ptr(fof), G.ptr(fob), G.ptr(ff),
+                                     G.stream_ptr(self._stream)), "fem_dof_maps")
+        return fof, fob, ff
+
+    def coords(self, which="bnd"):
+        w = 0 if which == "bnd" else 1
+        rows = self.n_bnd if w == 0 else self.n_free
+        out = torch.empty((rows, self.dim), dtype=torch.float64, device="cuda")
+        G.check(G.lib().fem_boundary_coords(self.handle, w, G.ptr(out), G.stream_ptr(self._stream)),
+                "fem_boundary_coords")
+        return out
+
+    def dirichlet(self, gid, coef=None, k=1, which="bnd"):
+        w = 0 if which == "bnd" else 1
+        rows = self.n_bnd if w == 0 else self.n_free
+        out = torch.empty((rows, k), dtype=torch.float64, device="cuda")
+        cp = None
+        if coef is not None:
+            import numpy as np
+            c = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+            cp = c.ctypes.data_as(C.POINTER(C.c_double))
+        G.check(G.lib().fem_dirichlet(self.handle, gid, cp, k, w, G.ptr(out), G.stream_ptr(self._stream)),
+                "fem_dirichlet")
+        return out
+
+    def lift(self, gB):
+        gB = gB.contiguous()
+        k = 1 if gB.dim() == 1 else gB.shape[1]
+        b = torch.empty((self.n_free, k), dtype=torch.float64, device="cuda")
+        G.check(G.lib().fem_lift_rhs(self.handle, G.ptr(gB), k, G.ptr(b), G.stream_ptr(self._stream)),
+                "fem_lift_rhs")
+        return b
+
+    def to_sell(self, C_=32, sigma=256, val_types=G.GB_VAL_F64 | G.GB_VAL_F32, stream=None):
+        h = C.c_void_p()
+        G.check(G.lib().csr_to_sell(self.handle, C_, sigma, val_types, G.torch_allocator(),
+                                    G.stream_ptr(stream if stream is not None else self._stream),
+                                    C.byref(h)), "csr_to_sell")
+        return Sell(h, stream if stream is not None else self._stream)
+
+
+class Sell:
+    """A SELL-C-sigma matrix (csr_to_sell / csr_to_sell_raw)."""
+
+    def __init__(self, handle, stream=None):
+        self.handle = handle
+        self._stream = stream
+        info = G.gb_sell_info()
+        G.check(G.lib().sell_info(handle, C.byref(info)), "sell_info")
+        self.info = info
+        self.n, self.nnz, self.padded, self.nchunks = info.n, info.nnz, info.padded, info.nchunks
+        self.C, self.sigma = info.C, info.sigma
+
+    @staticmethod
+    def from_csr(rowptr, col, val, C_=32, sigma=256, val_types=G.GB_VAL_F64 | G.GB_VAL_F32, stream=None):
+        h = C.c_void_p()
+        n = rowptr.numel() - 1
+        G.check(G.lib().csr_to_sell_raw(n, G.ptr(rowptr), G.ptr(col), G.ptr(val), C_, sigma, val_types,
+                                        G.torch_allocator(), G.stream_ptr(stream), C.byref(h)),
+                "csr_to_sell_raw")
+        return Sell(h, stream)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and G._lib is not None and not sys.is_finalizing():
+            torch.cuda.synchronize()
+            G._lib.sell_destroy(h)
+            self.handle = None
+
+    def structure(self):
+        i = self.info
+        return {"perm": _view(i.d_perm, (self.n,), torch.int32).clone(),
+                "chunk_ptr": _view(i.d_chunk_ptr, (self.nchunks + 1,), torch.int64).clone(),
+                "chunk_w": _view(i.d_chunk_w, (self.nchunks,), torch.int32).clone(),
+                "row_len": _view(i.d_row_len, (self.n,), torch.int32).clone(),
+                "col": _view(i.d_col, (self.padded,), torch.int32).clone(),
+                "val": _view(i.d_val, (self.padded,), torch.float64).clone(),
+                "dinv": _view(i.d_dinv, (self.n,), torch.float64).clone()}
+
+    def spmv(self, x):
+        y = torch.empty_like(x)
+        G.check(G.lib().sell_spmv(self.handle, G.ptr(x.contiguous()), G.ptr(y), G.stream_ptr(self._stream)),
+                "sell_spmv")
+        return y
+
+    def kernel_times(self, b, precision=G.GB_F64, iters=50, stream=None):
+        """pcg_kernel_times: mean ms of (SpMV + p.Ap, x/r update, p update)."""
+        ms = (C.c_double * 3)()
+        G.check(G.lib().pcg_kernel_times(self.handle, G.ptr(b.contiguous().reshape(-1)), precision, iters,
+                                         G.stream_ptr(stream if stream is not None else self._stream), ms),
+                "pcg_kernel_times")
+        return list(ms)
+
+    def solve(self, b, x0=None, raise_on_fail=True, stream=None, **kw):
+        """pcg_solve: returns (x, stats dict)."""
+        b = b.contiguous().reshape(-1)
+        x = x0.clone().reshape(-1) if x0 is not None else torch.empty_like(b)
+        o = _opts(x0_zero=0 if x0 is not None else 1, **kw)
+        st = G.PcgStats()
+        rc = G.lib().pcg_solve(self.handle, G.ptr(b), G.ptr(x), C.byref(o),
+                               G.stream_ptr(stream if stream is not None else self._stream), C.byref(st))
+        if raise_on_fail:
+            G.check(rc, "pcg_solve")
+        d = st.as_dict()
+        d["rc"] = rc
+        return x, d
+
+
+def pcg_solve_batched(mats, Bs, Xs=None, raise_on_fail=True, stream=None, **kw):
+    """pcg_solve_batched over Sell matrices with row-major (n, k) blocks."""
+    ns = len(mats)
+    Bs = [b.contiguous() if b.dim() == 2 else b.contiguous().reshape(-1, 1) for b in Bs]
+    if Xs is None:
+        Xs = [torch.empty_like(b) for b in Bs]
+        kw.setdefault("x0_zero", 1)
+    else:
+        Xs = [x.contiguous() if x.dim() == 2 else x.contiguous().reshape(-1, 1) for x in Xs]
+        kw.setdefault("x0_zero", 0)
+    A_arr = (C.c_void_p * ns)(*[m.handle.value for m in mats])
+    B_arr = (C.c_void_p * ns)(*[b.data_ptr() for b in Bs])
+    X_arr = (C.c_void_p * ns)(*[x.data_ptr() for x in Xs])
+    k_arr = (C.c_int * ns)(*[b.shape[1] for b in Bs])
+    o = _opts(**kw)
+    stats = (G.PcgStats * ns)()
+    rc = G.lib().pcg_solve_batched(ns, A_arr, B_arr, X_arr, k_arr, C.byref(o), G.stream_ptr(stream), stats)
+    if raise_on_fail:
+        G.check(rc, "pcg_solve_batched")
+    return Xs, [dict(s.as_dict(), rc=rc) for s in stats]

@@ -1,0 +1,683 @@
+// pcg.cu -- Jacobi-preconditioned CG on a SELL-C-sigma matrix, single RHS:
+// plain fp64, and fp32/bf16-inner iterative refinement with fp64 outer
+// residual, test and update.
+//
+// One iteration = three kernels (Hestenes-Stiefel order, as in the oracle):
+//   k_spmv_pq  q = A p and the partial sums of p.q; the last block to finish
+//              reduces the partials in a fixed order and sets alpha = rho/p.q
+//   k_update   x += alpha p, r -= alpha q, z = D^-1 r (never stored), partial
+//              sums of r.z and r.r; the last block sets beta, rho, tests
+//              ||r||^2 <= tol^2 ||b||^2 (Eq. 2) and the iteration cap
+//   k_pupdate  p = D^-1 r + beta p
+// The scalars live on the device, so the host never waits inside the loop:
+// the loop is a CUDA-graph while-node whose condition the finishing block
+// clears, or (use_graph=0) direct launches polled every few iterations.  Every
+// kernel returns at once when the recurrence is already done, so iterations
+// enqueued past convergence cost a launch each and nothing else.
+#include <cmath>
+#include <vector>
+
+#include "pcg.cuh"
+
+namespace gb {
+
+// ------------------------------------------------------------ kernels --
+template <class TV, class TX, int C>
+__global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict__ val,
+                                                const TX *__restrict__ p, TX *__restrict__ q,
+                                                double *partials, PcgScal *S) {
+    if (S->done) {
+        // a loop entered with the recurrence already finished must still end
+        if (blockIdx.x == 0 && threadIdx.x == 0 && S->use_cond) cudaGraphSetConditional(S->cond, 0);
+        return;
+    }
+    __shared__ double sm[NT / 32];
+    constexpr int SL = C / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)NT + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
+    const int64_t nsl = A.nchunks * SL;
+    TX dot = TX(0);
+    for (int64_t s = gw; s < nsl; s += nw) {
+        const int64_t c = s / SL;
+        const int sub = (int)(s - c * SL);
+        const int64_t r = c * C + sub * 32 + lane;
+        if (r >= A.n) continue;
+        const int L = A.row_len[r];
+        const int64_t base = A.chunk_ptr[c] + sub * 32 + lane;
+        const TV *v = val + base;
+        const int32_t *ci = A.col + base;
+        TX acc = TX(0);
+        int j = 0;
+        for (; j + 4 <= L; j += 4) {
+            const int c0 = ld_col(ci), c1 = ld_col(ci + C), c2 = ld_col(ci + 2 * C), c3 = ld_col(ci + 3 * C);
+            const TX v0 = (TX)ld_val(v), v1 = (TX)ld_val(v + C), v2 = (TX)ld_val(v + 2 * C), v3 = (TX)ld_val(v + 3 * C);
+            const TX p0 = p[c0], p1 = p[c1], p2 = p[c2], p3 = p[c3];
+            acc += v0 * p0;
+            acc += v1 * p1;
+            acc += v2 * p2;
+            acc += v3 * p3;
+            v += 4 * C;
+            ci += 4 * C;
+        }
+        for (; j < L; ++j) {
+            acc += (TX)ld_val(v) * p[ld_col(ci)];
+            v += C;
+            ci += C;
+        }
+        q[r] = acc;
+        dot += p[r] * acc;
+    }
+    const double t = block_sum<NT>((double)dot, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (arrive_last(&S->ticket)) {
+        const double pq = sum_partials(partials, gridDim.x, 1, 0, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) stop(S, ST_BREAK);
+            else S->alpha = S->rho / pq;
+        }
+    }
+}
+
+template <class TX, class TD>
+__global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX *__restrict__ r,
+                                               const TX *__restrict__ p, const TX *__restrict__ q,
+                                               const TD *__restrict__ dinv, double *partials,
+                                               PcgScal *S) {
+    if (S->done) return;
+    __shared__ double sm[NT / 32];
+    const TX alpha = (TX)S->alpha;
+    TX rz = TX(0), rr = TX(0);
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        const TX xi = x[i] + alpha * p[i];
+        const TX ri = r[i] - alpha * q[i];
+        const TX zi = (TX)dinv[i] * ri;
+        x[i] = xi;
+        r[i] = ri;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    const double a = block_sum<NT>((double)rz, sm);
+    const double b = block_sum<NT>((double)rr, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+    if (arrive_last(&S->ticket)) {
+        const double rz_t = sum_partials(partials, gridDim.x, 2, 0, sm);
+        const double rr_t = sum_partials(partials, gridDim.x, 2, 1, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->it += 1;
+            S->rr = rr_t;
+            if (!isfinite(rz_t) || !isfinite(rr_t)) stop(S, ST_BREAK);
+            else if (rr_t <= S->thresh) stop(S, ST_CONV);
+            else if (S->it >= S->maxit) stop(S, ST_MAXIT);
+            else {
+                S->beta = rz_t / S->rho;
+                S->rho = rz_t;
+            }
+        }
+    }
+}
+
+template <class TX, class TD>
+__global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, const TX *__restrict__ r,
+                                                const TD *__restrict__ dinv, const PcgScal *S) {
+    if (S->done) return;
+    const TX beta = (TX)S->beta;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+        p[i] = (TX)dinv[i] * r[i] + beta * p[i];
+}
+
+// r = b - A x (fp64, x optional = 0) with ||r||^2 and ||b||^2.  The last block
+// stores rr (and, when init, bb and the threshold tol^2 bb).
+template <int C>
+__global__ void __launch_bounds__(NT) k_residual(SellView A, const double *__restrict__ x,
+                                                 const double *__restrict__ b, double *__restrict__ r,
+                                                 double *partials, PcgScal *S, int init, double tol) {
+    __shared__ double sm[NT / 32];
+    constexpr int SL = C / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)NT + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * NT) >> 5;
+    double rr = 0.0, bb = 0.0;
+    for (int64_t s = gw; s < A.nchunks * SL; s += nw) {
+        const int64_t c = s / SL;
+        const int sub = (int)(s - c * SL);
+        const int64_t row = c * C + sub * 32 + lane;
+        if (row >= A.n) continue;
+        double acc = 0.0;
+        if (x) {
+            const int L = A.row_len[row];
+            const int64_t base = A.chunk_ptr[c] + sub * 32 + lane;
+            for (int j = 0; j < L; ++j) acc += ld_val(A.val + base + (int64_t)j * C) * x[ld_col(A.col + base + (int64_t)j * C)];
+        }
+        const double bi = b[row];
+        const double ri = bi - acc;
+        r[row] = ri;
+        rr += ri * ri;
+        bb += bi * bi;
+    }
+    const double a = block_sum<NT>(rr, sm);
+    const double c2 = block_sum<NT>(bb, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = c2;
+    }
+    if (arrive_last(&S->ticket)) {
+        const double rr_t = sum_partials(partials, gridDim.x, 2, 0, sm);
+        const double bb_t = sum_partials(partials, gridDim.x, 2, 1, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->rr = rr_t;
+            if (init) {
+                S->bb = bb_t;
+                S->thresh = tol * tol * bb_t;
+            }
+        }
+    }
+}
+
+// p = D^-1 r, rho = r.z; (re)starts the recurrence.
+template <class TX, class TD>
+__global__ void __launch_bounds__(NT) k_start(int64_t n, const TX *__restrict__ r, const TD *__restrict__ dinv,
+                                              TX *__restrict__ p, double *partials, PcgScal *S) {
+    __shared__ double sm[NT / 32];
+    double rz = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        const TX zi = (TX)dinv[i] * r[i];
+        p[i] = zi;
+        rz += (double)(r[i] * zi);
+    }
+    const double a = block_sum<NT>(rz, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+    if (arrive_last(&S->ticket)) {
+        const double t = sum_partials(partials, gridDim.x, 1, 0, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->rho = t;
+            S->done = 0;
+            S->status = ST_RUN;
+            if (!(t > 0.0)) { S->done = 1; S->status = t == 0.0 ? ST_CONV : ST_BREAK; }
+        }
+    }
+}
+
+__global__ void k_gather_d(int64_t n, const int32_t *perm, const double *src, double *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src ? src[perm[i]] : 0.0;
+}
+__global__ void k_scatter_d(int64_t n, const int32_t *perm, const double *src, double *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[perm[i]] = src[i];
+}
+// r32 = (float)(s * r64)
+__global__ void k_scale_down(int64_t n, const double *r, double s, float *r32, float *d32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        r32[i] = (float)(s * r[i]);
+        d32[i] = 0.0f;
+    }
+}
+// x += s * d
+__global__ void k_correct(int64_t n, double *x, double s, const float *d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += s * (double)d[i];
+}
+
+// ------------------------------------------------------------- driver --
+struct Grids {
+    int spmv, vec;
+};
+static Grids pick_grids(int64_t n, int C) {
+    const int sms = num_sms();
+    Grids g;
+    const int64_t warps = ((n + C - 1) / C) * (C / 32);
+    g.spmv = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (warps + 7) / 8));
+    g.vec = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (n + NT - 1) / NT));
+    return g;
+}
+
+template <class TV, class TX, class TD>
+static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
+                              TX *q, double *partials, PcgScal *S, const Grids &g, cudaStream_t st) {
+    switch (A.C) {
+    case 32: ::gb::count_launches(1); k_spmv_pq<TV, TX, 32><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
+    case 64: ::gb::count_launches(1); k_spmv_pq<TV, TX, 64><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
+    default: ::gb::count_launches(1); k_spmv_pq<TV, TX, 128><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
+    }
+    ::gb::count_launches(1); k_update<TX, TD><<<g.vec, NT, 0, st>>>(A.n, x, r, p, q, dinv, partials, S);
+    ::gb::count_launches(1); k_pupdate<TX, TD><<<g.vec, NT, 0, st>>>(A.n, p, r, dinv, S);
+}
+
+static void enqueue_residual(const SellView &A, const double *x, const double *b, double *r,
+                             double *partials, PcgScal *S, int init, double tol, const Grids &g,
+                             cudaStream_t st) {
+    switch (A.C) {
+    case 32: ::gb::count_launches(1); k_residual<32><<<g.spmv, NT, 0, st>>>(A, x, b, r, partials, S, init, tol); break;
+    case 64: ::gb::count_launches(1); k_residual<64><<<g.spmv, NT, 0, st>>>(A, x, b, r, partials, S, init, tol); break;
+    default: ::gb::count_launches(1); k_residual<128><<<g.spmv, NT, 0, st>>>(A, x, b, r, partials, S, init, tol); break;
+    }
+}
+
+// Runs the CG loop until the device flag says done.  Graph mode: one launch
+// of a graph holding a while-node around one iteration; the finishing block
+// clears the condition.  Direct mode: `chunk` iterations per host poll.
+template <class F>
+static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &&enqueue, int64_t *launches) {
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaStream_t cap = nullptr;
+        cudaGraphConditionalHandle h = 0;
+        GB_CHECK_CUDA(cudaGraphCreate(&g, 0));
+        int rc = GB_OK;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                set_capturing(true);
+                enqueue(cap);
+                set_capturing(false);
+                cudaGraph_t outg = nullptr;
+                e = cudaStreamEndCapture(cap, &outg);
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        long long it0 = 0, it1 = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&it0, &dS->it, sizeof(it0), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            struct { int use; cudaGraphConditionalHandle h; } hs{1, h};
+            e = cudaMemcpyAsync(&dS->use_cond, &hs.use, sizeof(int), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&dS->cond, &hs.h, sizeof(h), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+            int zero = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&dS->use_cond, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&it1, &dS->it, sizeof(it1), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            // the body ran once per iteration (plus once when it stopped inside SpMV)
+            count_launches(3 * (it1 - it0) + 3);
+        }
+        if (e != cudaSuccess) { set_error("pcg loop graph: %s", cudaGetErrorString(e)); rc = GB_ECUDA; }
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (cap) cudaStreamDestroy(cap);
+        (void)launches;
+        return rc;
+    }
+    for (;;) {
+        for (int i = 0; i < chunk; ++i) enqueue(st);
+        if (launches) *launches += 3 * chunk;
+        int done = 0;
+        GB_CHECK_CUDA(cudaGetLastError());
+        GB_CHECK_CUDA(cudaMemcpyAsync(&done, &dS->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (done) return GB_OK;
+    }
+}
+
+static PcgOptions defaults(const PcgOptions *o, int64_t n) {
+    PcgOptions d{};
+    if (o) d = *o;
+    if (!(d.tol > 0)) d.tol = 1e-10;
+    if (d.max_iter <= 0) d.max_iter = 20 * n + 100;
+    if (d.max_outer <= 0) d.max_outer = 30;
+    if (!(d.inner_tol > 0)) d.inner_tol = 1e-4;
+    if (d.check_every <= 0) d.check_every = (int)std::min<int64_t>(256, std::max<int64_t>(8, (1 << 20) / std::max<int64_t>(n, 1)));
+    return d;
+}
+
+static int read_scal(PcgScal *dS, PcgScal *h, cudaStream_t st) {
+    GB_CHECK_CUDA(cudaMemcpyAsync(h, dS, sizeof(PcgScal), cudaMemcpyDeviceToHost, st));
+    GB_CHECK_CUDA(cudaStreamSynchronize(st));
+    return GB_OK;
+}
+
+static int init_scal(PcgScal *dS, long long maxit, cudaStream_t st) {
+    PcgScal h{};
+    h.maxit = maxit;
+    GB_CHECK_CUDA(cudaMemcpyAsync(dS, &h, sizeof(PcgScal), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaStreamSynchronize(st));
+    return GB_OK;
+}
+
+static int map_status(int st) {
+    switch (st) {
+    case ST_CONV: return GB_OK;
+    case ST_BREAK: return GB_BREAKDOWN;
+    case ST_MAXIT: return GB_NOT_CONVERGED;
+    default: return GB_NOT_CONVERGED;
+    }
+}
+
+// Workspace of one single-RHS solve.
+struct Work {
+    Mem mem;
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partials = nullptr;
+    float *r32 = nullptr, *d32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    PcgScal *S = nullptr, *S2 = nullptr;
+    ~Work() {
+        mem.release(x); mem.release(r); mem.release(p); mem.release(q); mem.release(b);
+        mem.release(partials);
+        mem.release(r32); mem.release(d32); mem.release(p32); mem.release(q32);
+        mem.release(S); mem.release(S2);
+    }
+};
+
+}  // namespace gb
+
+using namespace gb;
+
+static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_t st, PcgStats *stats) {
+    const SellView V = A->view();
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    int64_t launches = 0;
+    // r = b - A x0, ||b||
+    enqueue_residual(V, o.x0_zero ? nullptr : w.x, w.b, w.r, w.partials, w.S, 1, o.tol, g, st);
+    ++launches;
+    PcgScal h{};
+    GB_TRY(read_scal(w.S, &h, st));
+    stats->bnorm = std::sqrt(h.bb);
+    if (h.bb == 0.0) {  // b = 0: x = 0
+        GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
+        stats->relres = 0.0;
+        stats->status = GB_OK;
+        stats->kernel_launches = launches + 1;
+        return GB_OK;
+    }
+    int64_t restarts = 0;
+    int status = ST_RUN;
+    double rel = std::sqrt(h.rr / h.bb);
+    while (rel > o.tol) {
+        ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
+        ++launches;
+        GB_CHECK_CUDA(cudaGetLastError());
+        auto body = [&](cudaStream_t s) {
+            enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.partials, w.S, g, s);
+        };
+        GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr));
+        GB_TRY(read_scal(w.S, &h, st));
+        status = h.status;
+        // confirm on the true residual (Eq. 2 is stated for b - A x)
+        enqueue_residual(V, w.x, w.b, w.r, w.partials, w.S, 0, o.tol, g, st);
+        ++launches;
+        PcgScal h2{};
+        GB_TRY(read_scal(w.S, &h2, st));
+        rel = std::sqrt(h2.rr / h2.bb);
+        if (status != ST_CONV || rel <= o.tol || h.it >= h.maxit || ++restarts > 50) break;
+    }
+    if (rel <= o.tol) status = ST_CONV;
+    stats->iterations = h.it;
+    stats->restarts = restarts;
+    stats->relres = rel;
+    stats->status = map_status(status);
+    stats->kernel_launches = launches + 3 * h.it;
+    const double bytes_iter = (double)A->nnz * 12.0 + 7.0 * n * 8.0;
+    stats->bytes_moved = bytes_iter * (double)h.it;
+    return GB_OK;
+}
+
+template <class TV>
+static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Work &w, cudaStream_t st,
+                    PcgStats *stats) {
+    const SellView V = A->view();
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    int64_t launches = 0;
+    Mem &mem = w.mem;
+    GB_TRY(mem.alloc_n(&w.r32, n));
+    GB_TRY(mem.alloc_n(&w.d32, n));
+    GB_TRY(mem.alloc_n(&w.p32, n));
+    GB_TRY(mem.alloc_n(&w.q32, n));
+    GB_TRY(mem.alloc_n(&w.S2, 1));
+    enqueue_residual(V, o.x0_zero ? nullptr : w.x, w.b, w.r, w.partials, w.S, 1, o.tol, g, st);
+    ++launches;
+    PcgScal h{};
+    GB_TRY(read_scal(w.S, &h, st));
+    stats->bnorm = std::sqrt(h.bb);
+    if (h.bb == 0.0) {
+        GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
+        stats->relres = 0.0;
+        stats->status = GB_OK;
+        return GB_OK;
+    }
+    double rel = std::sqrt(h.rr / h.bb);
+    int outer = 0;
+    int64_t inner_total = 0;
+    double prev = rel;
+    int stalls = 0;
+    int status = ST_RUN;
+    const double sval = sizeof(TV);
+    double bytes = 0.0;
+    while (rel > o.tol && outer < o.max_outer && inner_total < o.max_iter) {
+        ++outer;
+        const double rn = std::sqrt(h.rr);
+        // inner system A d = r / ||r|| in fp32, from d = 0
+        ::gb::count_launches(1); k_scale_down<<<g.vec, NT, 0, st>>>(n, w.r, 1.0 / rn, w.r32, w.d32);
+        {
+            // ||r32||^2 ~ 1: threshold from the inner tolerance
+            PcgScal hs{};
+            hs.maxit = o.max_iter - inner_total;
+            hs.bb = 1.0;
+            hs.thresh = o.inner_tol * o.inner_tol;
+            GB_CHECK_CUDA(cudaMemcpyAsync(w.S2, &hs, sizeof(PcgScal), cudaMemcpyHostToDevice, st));
+        }
+        ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
+        launches += 2;
+        auto body = [&](cudaStream_t s) {
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s);
+        };
+        GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
+        PcgScal hi{};
+        GB_TRY(read_scal(w.S2, &hi, st));
+        inner_total += hi.it;
+        launches += 3 * hi.it;
+        bytes += hi.it * ((double)A->nnz * (sval + 4.0) + 7.0 * n * 4.0);
+        // x += ||r|| d ; r = b - A x in fp64
+        ::gb::count_launches(1); k_correct<<<g.vec, NT, 0, st>>>(n, w.x, rn, w.d32);
+        enqueue_residual(V, w.x, w.b, w.r, w.partials, w.S, 0, o.tol, g, st);
+        launches += 2;
+        bytes += (double)A->nnz * 12.0 + 5.0 * n * 8.0;
+        GB_TRY(read_scal(w.S, &h, st));
+        rel = std::sqrt(h.rr / h.bb);
+        if (!(rel < 0.9 * prev)) { if (++stalls >= 2) break; } else stalls = 0;
+        prev = std::min(prev, rel);
+        if (hi.status == ST_BREAK && hi.it == 0) break;
+    }
+    status = rel <= o.tol ? ST_CONV : ST_MAXIT;
+    stats->iterations = inner_total;
+    stats->outer = outer;
+    stats->relres = rel;
+    stats->status = map_status(status);
+    stats->kernel_launches = launches;
+    stats->bytes_moved = bytes;
+    return GB_OK;
+}
+
+extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
+                         void *stream, PcgStats *stats) {
+    GB_REQUIRE(A && d_b && d_x, "pcg_solve: NULL argument");
+    PcgStats dummy{};
+    if (!stats) stats = &dummy;
+    *stats = PcgStats{};
+    PcgOptions o = defaults(opt, A->n);
+    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve: bad precision");
+    GB_REQUIRE(o.precision != GB_F32_IR || A->val32, "pcg_solve: F32_IR needs fp32 values (val_types)");
+    GB_REQUIRE(o.precision != GB_BF16_IR || A->val16, "pcg_solve: BF16_IR needs bf16 values (val_types)");
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    w.mem = Mem(nullptr, st);
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    GB_TRY(w.mem.alloc_n(&w.x, n));
+    GB_TRY(w.mem.alloc_n(&w.r, n));
+    GB_TRY(w.mem.alloc_n(&w.p, n));
+    GB_TRY(w.mem.alloc_n(&w.q, n));
+    GB_TRY(w.mem.alloc_n(&w.b, n));
+    GB_TRY(w.mem.alloc_n(&w.partials, 2 * (size_t)std::max(g.spmv, g.vec)));
+    GB_TRY(w.mem.alloc_n(&w.S, 1));
+    GB_TRY(init_scal(w.S, o.max_iter, st));
+    cudaEvent_t e0, e1;
+    GB_CHECK_CUDA(cudaEventCreate(&e0));
+    GB_CHECK_CUDA(cudaEventCreate(&e1));
+    GB_CHECK_CUDA(cudaEventRecord(e0, st));
+    ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
+    ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, o.x0_zero ? nullptr : d_x, w.x);
+    int rc;
+    if (o.precision == GB_F64) rc = solve_f64(A, o, w, st, stats);
+    else if (o.precision == GB_F32_IR) rc = solve_ir<float>(A, A->val32, o, w, st, stats);
+    else rc = solve_ir<__nv_bfloat16>(A, A->val16, o, w, st, stats);
+    if (rc == GB_OK && o.precision != GB_F64 && stats->status != GB_OK && stats->iterations < o.max_iter) {
+        // refinement stalled above tol: finish in fp64 from the current x
+        PcgOptions o2 = o;
+        o2.x0_zero = 0;
+        o2.max_iter = o.max_iter - stats->iterations;
+        PcgStats s2{};
+        rc = init_scal(w.S, o2.max_iter, st);
+        if (rc == GB_OK) rc = solve_f64(A, o2, w, st, &s2);
+        if (rc == GB_OK) {
+            stats->fallback_iterations = s2.iterations;
+            stats->relres = s2.relres;
+            stats->status = s2.status;
+            stats->kernel_launches += s2.kernel_launches;
+            stats->bytes_moved += s2.bytes_moved;
+        }
+    }
+    if (rc == GB_OK) {
+        ::gb::count_launches(1); k_scatter_d<<<g.vec, NT, 0, st>>>(n, A->perm, w.x, d_x);
+        stats->kernel_launches += 3;
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        stats->solve_ms = ms;
+        if (e != cudaSuccess) { set_error("pcg_solve: %s", cudaGetErrorString(e)); rc = GB_ECUDA; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GB_OK) return rc;
+    if (stats->status != GB_OK) {
+        set_error("pcg_solve: %s after %lld iterations (relres %.3e)",
+                  stats->status == GB_BREAKDOWN ? "breakdown" : "not converged",
+                  (long long)stats->iterations, stats->relres);
+        return stats->status;
+    }
+    return GB_OK;
+}
+
+extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters,
+                                void *stream, double *h_ms) {
+    GB_REQUIRE(A && d_b && h_ms, "pcg_kernel_times: NULL argument");
+    GB_REQUIRE(iters >= 1 && iters <= 100000, "pcg_kernel_times: iters must be in 1..100000");
+    GB_REQUIRE(precision >= GB_F64 && precision <= GB_BF16_IR, "pcg_kernel_times: bad precision");
+    GB_REQUIRE(precision != GB_F32_IR || A->val32, "pcg_kernel_times: no fp32 values");
+    GB_REQUIRE(precision != GB_BF16_IR || A->val16, "pcg_kernel_times: no bf16 values");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    const SellView V = A->view();
+    Work w;
+    w.mem = Mem(nullptr, st);
+    GB_TRY(w.mem.alloc_n(&w.x, n));
+    GB_TRY(w.mem.alloc_n(&w.r, n));
+    GB_TRY(w.mem.alloc_n(&w.p, n));
+    GB_TRY(w.mem.alloc_n(&w.q, n));
+    GB_TRY(w.mem.alloc_n(&w.b, n));
+    GB_TRY(w.mem.alloc_n(&w.r32, n));
+    GB_TRY(w.mem.alloc_n(&w.d32, n));
+    GB_TRY(w.mem.alloc_n(&w.p32, n));
+    GB_TRY(w.mem.alloc_n(&w.q32, n));
+    GB_TRY(w.mem.alloc_n(&w.partials, 2 * (size_t)std::max(g.spmv, g.vec)));
+    GB_TRY(w.mem.alloc_n(&w.S, 1));
+    PcgScal hs{};
+    hs.maxit = (long long)iters + 1;
+    hs.thresh = -1.0;  // never converges: every timed launch is a full pass
+    GB_CHECK_CUDA(cudaMemcpyAsync(w.S, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
+    GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
+    enqueue_residual(V, nullptr, w.b, w.r, w.partials, w.S, 0, 0.0, g, st);
+    if (precision == GB_F64) {
+        ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
+    } else {
+        ::gb::count_launches(1); k_scale_down<<<g.vec, NT, 0, st>>>(n, w.r, 1.0, w.r32, w.d32);
+        ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S);
+    }
+    GB_CHECK_CUDA(cudaGetLastError());
+    std::vector<cudaEvent_t> ev(3 * (size_t)iters + 1);
+    for (auto &e : ev) GB_CHECK_CUDA(cudaEventCreate(&e));
+    int rc = GB_OK;
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < iters; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            if (precision == GB_F64) {
+                if (k == 0) {
+                    switch (A->C) {
+                    case 32: ::gb::count_launches(1); k_spmv_pq<double, double, 32><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
+                    case 64: ::gb::count_launches(1); k_spmv_pq<double, double, 64><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
+                    default: ::gb::count_launches(1); k_spmv_pq<double, double, 128><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
+                    }
+                } else if (k == 1) {
+                    ::gb::count_launches(1); k_update<double, double><<<g.vec, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.partials, w.S);
+                } else {
+                    ::gb::count_launches(1); k_pupdate<double, double><<<g.vec, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.S);
+                }
+            } else {
+                if (k == 0) {
+                    if (precision == GB_F32_IR) {
+                        switch (A->C) {
+                        case 32: ::gb::count_launches(1); k_spmv_pq<float, float, 32><<<g.spmv, NT, 0, st>>>(V, A->val32, w.p32, w.q32, w.partials, w.S); break;
+                        case 64: ::gb::count_launches(1); k_spmv_pq<float, float, 64><<<g.spmv, NT, 0, st>>>(V, A->val32, w.p32, w.q32, w.partials, w.S); break;
+                        default: ::gb::count_launches(1); k_spmv_pq<float, float, 128><<<g.spmv, NT, 0, st>>>(V, A->val32, w.p32, w.q32, w.partials, w.S); break;
+                        }
+                    } else {
+                        switch (A->C) {
+                        case 32: ::gb::count_launches(1); k_spmv_pq<__nv_bfloat16, float, 32><<<g.spmv, NT, 0, st>>>(V, A->val16, w.p32, w.q32, w.partials, w.S); break;
+                        case 64: ::gb::count_launches(1); k_spmv_pq<__nv_bfloat16, float, 64><<<g.spmv, NT, 0, st>>>(V, A->val16, w.p32, w.q32, w.partials, w.S); break;
+                        default: ::gb::count_launches(1); k_spmv_pq<__nv_bfloat16, float, 128><<<g.spmv, NT, 0, st>>>(V, A->val16, w.p32, w.q32, w.partials, w.S); break;
+                        }
+                    }
+                } else if (k == 1) {
+                    ::gb::count_launches(1); k_update<float, float><<<g.vec, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, w.partials, w.S);
+                } else {
+                    ::gb::count_launches(1); k_pupdate<float, float><<<g.vec, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, w.S);
+                }
+            }
+            cudaEventRecord(ev[3 * (size_t)i + k + 1], st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    double tot[3] = {0, 0, 0};
+    for (int i = 0; i < iters && e == cudaSuccess; ++i)
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[3 * (size_t)i + k], ev[3 * (size_t)i + k + 1]);
+            tot[k] += ms;
+        }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) { set_error("pcg_kernel_times: %s", cudaGetErrorString(e)); return GB_ECUDA; }
+    PcgScal h{};
+    GB_TRY(read_scal(w.S, &h, st));
+    if (h.done) {
+        set_error("pcg_kernel_times: the recurrence stopped (status %d) after %lld iterations; use fewer",
+                  h.status, h.it);
+        rc = GB_BREAKDOWN;
+    }
+    for (int k = 0; k < 3; ++k) h_ms[k] = tot[k] / iters;
+    return rc;
+}

@@ -1,0 +1,65 @@
+// pcg.cuh -- device-side Jacobi-PCG building blocks shared by the single-,
+// multi-RHS and batched solvers.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "sell.cuh"
+
+namespace gb {
+
+constexpr int NT = 256;  // threads per block of every solver kernel
+
+// Device-resident scalars of one CG recurrence (fp64 whatever the vector type).
+struct PcgScal {
+    double rho;     // r.z
+    double pq;      // p.Ap
+    double alpha, beta;
+    double rr;      // ||r||^2 (recursive)
+    double bb;      // ||b||^2
+    double thresh;  // tol^2 ||b||^2
+    long long it, maxit;
+    int done, status;
+    unsigned int ticket;  // last-block counter
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+};
+enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3 };
+
+// Streaming loads for the matrix (read once per iteration: evict first).
+__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_val(const __nv_bfloat16 *p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short *>(p));
+    return __uint_as_float(((unsigned int)u) << 16);
+}
+__device__ __forceinline__ int ld_col(const int32_t *p) { return __ldcs(p); }
+
+// True in every thread of the block that arrives last at `ticket` (after all
+// other blocks have published their partial sums).
+__device__ __forceinline__ bool arrive_last(unsigned int *ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Deterministic sum of partials[i*stride+off], i < G (fixed order per thread,
+// fixed tree across threads).  Valid in thread 0; all threads must call.
+__device__ __forceinline__ double sum_partials(const double *partials, int G, int stride, int off,
+                                               double *smem) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < G; i += NT) s += __ldcg(partials + (size_t)i * stride + off);
+    return block_sum<NT>(s, smem);
+}
+
+__device__ __forceinline__ void stop(PcgScal *S, int status) {
+    S->status = status;
+    S->done = 1;
+    if (S->use_cond) cudaGraphSetConditional(S->cond, 0);
+}
+
+}  // namespace gb

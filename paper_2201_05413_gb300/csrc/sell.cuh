@@ -1,0 +1,37 @@
+// sell.cuh -- SELL-C-sigma matrix object shared by the builder and the solvers.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gb {
+
+// Plain view passed by value to kernels.
+struct SellView {
+    int64_t n, nchunks;
+    int C;
+    const int64_t *chunk_ptr;
+    const int32_t *row_len;
+    const int32_t *col;
+    const double *val;
+    const float *val32;
+    const __nv_bfloat16 *val16;
+    const double *dinv;
+    const float *dinv32;
+};
+
+}  // namespace gb
+
+struct gb_sell {
+    int64_t n = 0, nnz = 0, padded = 0, nchunks = 0;
+    int C = 32, sigma = 1, max_row = 0;
+    int32_t *perm = nullptr, *iperm = nullptr, *row_len = nullptr, *chunk_w = nullptr, *col = nullptr;
+    int64_t *chunk_ptr = nullptr;
+    double *val = nullptr, *dinv = nullptr;
+    float *val32 = nullptr, *dinv32 = nullptr;
+    __nv_bfloat16 *val16 = nullptr;
+    gb::Mem mem;
+    gb::SellView view() const {
+        return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32};
+    }
+};

@@ -1,0 +1,104 @@
+"""GPU parity: pcg_solve_batched -- blocked multi-RHS PCG (Eq. MRH, Sec. 4.3)
+and several uneven systems in the same launches, fp64 and fp32-inner
+refinement, against the oracle column by column."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_05413_gb300 as P
+    P.load()
+    return P
+
+
+def _oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k):
+    s = O.System(dim, deg, cells, jit, dm, seed).assemble()
+    rp, ci, v = s.k_ii()
+    B = s.lift(s.eval_g(gid, coef, k, "bnd"))
+    X = np.stack([O.pcg(rp, ci, v, B[:, j], tol=1e-13)[0] for j in range(k)], 1)
+    return s, rp, ci, v, B, X
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 32])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_multi_rhs_matches_oracle(P, k, prec):
+    spec = (2, 2, 24, 1, 1, 2)
+    coef = np.random.default_rng(3).standard_normal((k, 10))
+    d = P.FemSystem(*spec)
+    A = d.to_sell(32, 256)
+    B = d.lift(d.dirichlet(O.G_HARMONIC, coef, k))
+    p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
+    Xs, stats = P.pcg_solve_batched([A], [B], tol=TOL, precision=p, max_iter=100000)
+    X = Xs[0].cpu().numpy()
+    s, rp, ci, v, Bo, Xo = _oracle_cols(*spec, O.G_HARMONIC, coef, k)
+    for j in range(k):
+        rel = np.linalg.norm(Bo[:, j] - O.spmv(rp, ci, v, X[:, j])) / np.linalg.norm(Bo[:, j])
+        assert rel <= 1.5 * TOL, (j, rel)
+        assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8, j
+    assert stats[0]["status"] == 0 and stats[0]["relres"] <= TOL
+
+
+def test_uneven_systems_one_batch(P):
+    specs = [(2, 1, 20, 1, 1, 1, 1), (2, 2, 13, 1, 1, 2, 3), (3, 1, 9, 0, 0, 0, 2), (3, 2, 5, 0, 0, 0, 5)]
+    mats, Bs, refs = [], [], []
+    rng = np.random.default_rng(7)
+    for dim, deg, cells, jit, dm, seed, k in specs:
+        d = P.FemSystem(dim, deg, cells, jit, dm, seed)
+        gid = O.G_HARMONIC if dim == 2 else O.G_LINEAR
+        coef = rng.standard_normal((k, O.NCOEF[gid]))
+        mats.append(d.to_sell(32, 64))
+        Bs.append(d.lift(d.dirichlet(gid, coef, k)))
+        refs.append(_oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k))
+    Xs, stats = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=100000)
+    for X, (s, rp, ci, v, Bo, Xo), st in zip(Xs, refs, stats):
+        X = X.cpu().numpy()
+        assert st["status"] == 0
+        for j in range(X.shape[1]):
+            assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8
+    # each result equals the same system solved alone, bit for bit
+    for i in range(len(mats)):
+        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, max_iter=100000)
+        assert bool((Xa[0] == Xs[i]).all())
+        assert sa[0]["iterations"] == stats[i]["iterations"]
+
+
+def test_batched_k1_matches_single_solve(P):
+    d = P.FemSystem(2, 2, 20, 1, 1, 4)
+    A = d.to_sell(32, 256)
+    b = d.lift(d.dirichlet(1))
+    Xs, st = P.pcg_solve_batched([A], [b], tol=TOL)
+    x, st1 = A.solve(b[:, 0], tol=TOL)
+    assert abs(st[0]["iterations"] - st1["iterations"]) <= 2
+    assert O.x_err(x.cpu().numpy(), Xs[0][:, 0].cpu().numpy()) < 1e-8
+
+
+def test_batched_direct_launch_mode(P):
+    d = P.FemSystem(2, 1, 30, 1, 1, 4)
+    A = d.to_sell()
+    coef = np.random.default_rng(0).standard_normal((4, 10))
+    B = d.lift(d.dirichlet(O.G_HARMONIC, coef, 4))
+    X1, s1 = P.pcg_solve_batched([A], [B], use_graph=1)
+    X2, s2 = P.pcg_solve_batched([A], [B], use_graph=0, check_every=5)
+    assert bool((X1[0] == X2[0]).all()) and s1[0]["iterations"] == s2[0]["iterations"]
+
+
+def test_batched_zero_column_and_errors(P):
+    import torch
+    d = P.FemSystem(2, 1, 12, 1, 1, 4)
+    A = d.to_sell()
+    B = d.lift(d.dirichlet(O.G_HARMONIC, np.ones((3, 10)), 3))
+    B[:, 1] = 0
+    Xs, st = P.pcg_solve_batched([A], [B])
+    assert torch.count_nonzero(Xs[0][:, 1]).item() == 0
+    with pytest.raises(P.GbError):
+        P.pcg_solve_batched([A], [torch.zeros((d.n_free, 33), dtype=torch.float64, device="cuda")])
