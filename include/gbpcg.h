@@ -224,6 +224,27 @@ int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_
                       double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                       PcgStats *stats);
 
+/* pcg_solve_noalloc -- the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory: code running inside another
+ * allocator's callbacks, in a process whose device memory belongs to a fixed
+ * arena that must not grow, or in a loop that may not block on cudaMalloc.
+ * It is pcg_solve with precision GB_F64 only, but it allocates nothing: its
+ * scratch (permuted b and x, r, p, q, partial sums, solver scalars) lives in a
+ * file-scope device array sized for at most 262144 rows (about 10.5 MB),
+ * which every GPU that loads the library holds until the process exits.
+ * The caller still passes A, d_b and d_x (n doubles each, x in: x0 unless
+ * opt->x0_zero).  Larger systems return GB_TOO_LARGE with a message naming the
+ * limit; other precisions return GB_EINVAL.  The CG loop is always direct
+ * launches polled from the host (opt->use_graph is ignored), the call
+ * synchronises `stream`, and stats->solve_ms is host wall time.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  All calls share the one array and the solver scalars are
+ * reset at the start of every call; two calls whose work overlaps on the GPU
+ * (different streams or threads) race on that array and give wrong results. */
+int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
+                      void *stream, PcgStats *stats);
+
 /* Measurement entry point (no counterpart in the paper): runs `iters` fp64
  * (precision GB_F64) or fp32-inner (GB_F32_IR / GB_BF16_IR) CG iterations on
  * A with right-hand side d_b from x = 0, as direct launches on `stream`, with

@@ -14,7 +14,9 @@
 // clears, or (use_graph=0) direct launches polled every few iterations.  Every
 // kernel returns at once when the recurrence is already done, so iterations
 // enqueued past convergence cost a launch each and nothing else.
+#include <chrono>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "pcg.cuh"
@@ -680,4 +682,107 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
     }
     for (int k = 0; k < 3; ++k) h_ms[k] = tot[k] / iters;
     return rc;
+}
+
+// ------------------------------------------------------- no-allocation solve --
+// pcg_solve_noalloc: the fp64 pcg_solve for callers that cannot allocate
+// device memory -- code that runs where cudaMalloc is forbidden or unsafe
+// (inside another allocator's callbacks, in a process whose device memory is
+// owned by a fixed arena it must not grow, in a real-time loop that may not
+// block on the allocator).  Its scratch (the permuted b and x, r, p, q, the
+// per-block partial sums and the solver scalars) lives in one file-scope
+// device array of fixed size, so the call allocates nothing: it enqueues
+// kernels, copies the few solver scalars back to the host and synchronises.
+namespace gb {
+constexpr int64_t NOALLOC_MAX_N = 262144;  // rows
+constexpr int64_t NOALLOC_PARTIALS = 4096;  // doubles: 2 per block, up to 256 SMs x 8 blocks
+constexpr size_t NOALLOC_BYTES = (size_t)5 * NOALLOC_MAX_N * sizeof(double) +
+                                 NOALLOC_PARTIALS * sizeof(double) + 256;
+// Every GPU that loads this library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Host code must not take the address of g_noalloc_scratch directly (that is
+// a host-side stand-in); the device address is looked up once per device.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128] = {};
+
+static int noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    GB_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) { set_error("pcg_solve_noalloc: device %d out of range", dev); return GB_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("pcg_solve_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return GB_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (unsigned char *)g_noalloc_ptr[dev];
+    return GB_OK;
+}
+}  // namespace gb
+
+extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
+                                 void *stream, PcgStats *stats) {
+    GB_REQUIRE(A && d_b && d_x, "pcg_solve_noalloc: NULL argument");
+    if (A->n > NOALLOC_MAX_N) {
+        set_error("pcg_solve_noalloc: n = %lld rows exceeds the fixed scratch limit of %lld rows; use pcg_solve",
+                  (long long)A->n, (long long)NOALLOC_MAX_N);
+        return GB_TOO_LARGE;
+    }
+    PcgStats dummy{};
+    if (!stats) stats = &dummy;
+    *stats = PcgStats{};
+    PcgOptions o = defaults(opt, A->n);
+    GB_REQUIRE(o.precision == GB_F64, "pcg_solve_noalloc: only precision GB_F64 is available");
+    o.use_graph = 0;  // graph objects would allocate: the loop is polled direct launches
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    if (2 * (int64_t)std::max(g.spmv, g.vec) > NOALLOC_PARTIALS) {
+        set_error("pcg_solve_noalloc: this device needs %d partial sums, above the fixed %lld",
+                  2 * std::max(g.spmv, g.vec), (long long)NOALLOC_PARTIALS);
+        return GB_TOO_LARGE;
+    }
+    unsigned char *base = nullptr;
+    GB_TRY(noalloc_scratch(&base));
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;  // views into the static array; nothing here is released
+    w.mem = Mem(nullptr, st);
+    double *vec = (double *)base;
+    w.x = vec;
+    w.r = vec + NOALLOC_MAX_N;
+    w.p = vec + 2 * NOALLOC_MAX_N;
+    w.q = vec + 3 * NOALLOC_MAX_N;
+    w.b = vec + 4 * NOALLOC_MAX_N;
+    w.partials = vec + 5 * NOALLOC_MAX_N;
+    w.S = (PcgScal *)(base + (size_t)5 * NOALLOC_MAX_N * sizeof(double) + NOALLOC_PARTIALS * sizeof(double));
+    static_assert(sizeof(PcgScal) <= 256, "solver scalars must fit the reserved tail");
+    int rc = init_scal(w.S, o.max_iter, st);  // the scalars (and the block ticket) start from zero
+    const auto t0 = std::chrono::steady_clock::now();
+    if (rc == GB_OK) {
+        ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
+        ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, o.x0_zero ? nullptr : d_x, w.x);
+        rc = solve_f64(A, o, w, st, stats);
+    }
+    if (rc == GB_OK) {
+        ::gb::count_launches(1); k_scatter_d<<<g.vec, NT, 0, st>>>(n, A->perm, w.x, d_x);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { set_error("pcg_solve_noalloc: %s", cudaGetErrorString(e)); rc = GB_ECUDA; }
+        stats->kernel_launches += 3;
+    }
+    stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    w.x = w.r = w.p = w.q = w.b = w.partials = nullptr;
+    w.S = nullptr;
+    if (rc != GB_OK) return rc;
+    if (stats->status != GB_OK) {
+        set_error("pcg_solve_noalloc: %s after %lld iterations (relres %.3e)",
+                  stats->status == GB_BREAKDOWN ? "breakdown" : "not converged",
+                  (long long)stats->iterations, stats->relres);
+        return stats->status;
+    }
+    return GB_OK;
 }

@@ -93,6 +93,7 @@ _SIGS = {
     "sell_spmv": (C.c_int, [_P, _P, _P, _P]),
     "sell_destroy": (None, [_P]),
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
+    "pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_kernel_times": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_double)]),
     "pcg_solve_batched": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                     C.POINTER(C.c_int), C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),

@@ -1,0 +1,83 @@
+"""pcg_solve_noalloc: the fp64 solve for callers that cannot allocate device
+memory (its scratch is a fixed file-scope device array).  Called through the
+C ABI and compared with pcg_solve on the same system, twice in a row (the
+second call reuses the array the first one left behind).  This file sorts last
+so that a run stopping at the first failure has run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+XERR = 1e-8   # relative error bar of the solver tests
+TOL = 1e-10   # Eq. (2) residual threshold
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2201_05413_gb300 as P
+    P.load()
+    return P
+
+
+def _noalloc(P, A, b, x0=None, **kw):
+    import torch
+    from paper_2201_05413_gb300 import gbpcg as G
+    from paper_2201_05413_gb300.api import _opts
+    x = x0.clone() if x0 is not None else torch.full_like(b, float("nan"))
+    o = _opts(x0_zero=0 if x0 is not None else 1, **kw)
+    st = G.PcgStats()
+    rc = G.lib().pcg_solve_noalloc(A.handle, G.ptr(b), G.ptr(x), C.byref(o), G.stream_ptr(), C.byref(st))
+    return rc, x, st
+
+
+def _xerr(a, b):
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(a))
+
+
+@pytest.mark.parametrize("spec", [(2, 2, 200, 1, 1, 3), (3, 1, 40, 0, 0, 0)])
+def test_noalloc_matches_pcg_solve_twice(P, spec):
+    d = P.FemSystem(*spec)
+    assert d.n_free <= 262144
+    A = d.to_sell(32, 256)
+    gid = 1 if spec[0] == 2 else 2
+    b = d.lift(d.dirichlet(gid))[:, 0].contiguous()
+    x_ref, st_ref = A.solve(b, tol=TOL, max_iter=200000)
+    for _ in range(2):
+        rc, x, st = _noalloc(P, A, b, tol=TOL, max_iter=200000)
+        assert rc == 0, P.gbpcg.lib().gbpcg_last_error()
+        assert st.status == 0 and st.relres <= TOL
+        assert _xerr(x_ref, x) <= XERR
+        assert abs(st.iterations - st_ref["iterations"]) <= 2
+
+
+def test_noalloc_second_system_after_first(P):
+    """A smaller system after a larger one: nothing stale from the first call leaks in."""
+    d1 = P.FemSystem(2, 1, 400, 1, 1, 1)
+    d2 = P.FemSystem(2, 2, 30, 1, 1, 2)
+    for d in (d1, d2):
+        A = d.to_sell()
+        b = d.lift(d.dirichlet(1))[:, 0].contiguous()
+        x_ref, _ = A.solve(b, tol=TOL)
+        rc, x, st = _noalloc(P, A, b, tol=TOL)
+        assert rc == 0 and _xerr(x_ref, x) <= XERR
+
+
+def test_noalloc_rejects_oversized_and_other_precisions(P):
+    from paper_2201_05413_gb300 import gbpcg as G
+    d = P.FemSystem(2, 1, 600)  # 599^2 = 358801 rows > 262144
+    A = d.to_sell()
+    b = d.lift(d.dirichlet(1))[:, 0].contiguous()
+    rc, x, st = _noalloc(P, A, b)
+    assert rc == G.GB_TOO_LARGE
+    assert b"262144" in G.lib().gbpcg_last_error()
+    small = P.FemSystem(2, 1, 20)
+    As = small.to_sell()
+    bs = small.lift(small.dirichlet(1))[:, 0].contiguous()
+    rc, x, st = _noalloc(P, As, bs, precision=G.GB_F32_IR)
+    assert rc == G.GB_EINVAL
