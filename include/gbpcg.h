@@ -180,19 +180,24 @@ void sell_destroy(gb_sell *A);
  * relative residual inner_tol.  If the refinement stalls (two outer steps
  * without a 10% residual reduction) or runs out of outer steps above tol, the
  * solve continues with fp64 PCG from the current x on the device, and
- * stats.fallback_iterations counts those iterations. */
-enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2 };
+ * stats.fallback_iterations counts those iterations.
+ * GB_F32_RU / GB_BF16_RU: the same split of precisions with reliable updates
+ * instead of restarts -- one fp32 recurrence keeps its search direction; each
+ * time its residual has dropped tenfold, x += d and r = b - A x are formed in
+ * fp64, the test is made in fp64 and the fp32 residual is replaced by the
+ * true one (stats.outer counts these updates).  pcg_solve only. */
+enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2, GB_F32_RU = 3, GB_BF16_RU = 4 };
 
 typedef struct PcgOptions {
     double tol;            /* Eq. (2) threshold, e.g. 1e-10 */
     int64_t max_iter;      /* total (inner) iterations cap; 0 = 20 n + 100 */
-    int32_t precision;     /* GB_F64 | GB_F32_IR | GB_BF16_IR */
+    int32_t precision;     /* GB_F64 | GB_F32_IR | GB_BF16_IR | GB_F32_RU | GB_BF16_RU */
     int32_t max_outer;     /* refinement steps cap (IR only); 0 = 30 */
     double inner_tol;      /* inner relative residual (IR only); 0 = 1e-4 */
     int32_t check_every;   /* iterations per host convergence poll; 0 = auto */
     int32_t use_graph;     /* 1 = replay captured CUDA graphs (default), 0 = direct launches */
     int32_t x0_zero;       /* 1 = ignore d_x on entry and start from 0 */
-    int32_t reserved;
+    int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
 } PcgOptions;
 
 typedef struct PcgStats {

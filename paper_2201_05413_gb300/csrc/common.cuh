@@ -87,6 +87,11 @@ int scan_exclusive(const In *in, Out *out, int64_t n, int64_t *h_total, Mem &mem
 
 // ------------------------------------------------------- launch geometry --
 int num_sms();
+// blocks per SM of the TMA-staged SpMV (fixed: its warp partition is built for it)
+#ifndef GB_TMA_BLOCKS_PER_SM
+#define GB_TMA_BLOCKS_PER_SM 4
+#endif
+constexpr int TMA_BLOCKS_PER_SM = GB_TMA_BLOCKS_PER_SM;
 // Grid for a grid-stride kernel: a multiple of the SM count, at most `want`.
 inline int stride_grid(int64_t work_items, int block, int per_sm) {
     int sms = num_sms();

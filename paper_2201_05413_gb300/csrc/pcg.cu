@@ -20,8 +20,62 @@
 #include <vector>
 
 #include "pcg.cuh"
+#include "spmv_tma.cuh"
 
 namespace gb {
+
+// q = A p with TMA-staged slices (spmv_tma.cuh), one warp per balanced chunk
+// range, then the same p.q reduction and alpha as k_spmv_pq.
+template <class TV, class TX>
+__global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restrict__ val,
+                                                 const TX *__restrict__ p, TX *__restrict__ q,
+                                                 double *partials, PcgScal *S) {
+    if (S->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && S->use_cond) cudaGraphSetConditional(S->cond, 0);
+        return;
+    }
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double sm[NT / 32];
+    constexpr int NB = TmaDepth<TV>::NB;
+    TmaRing<TV, NB> *bufs = reinterpret_cast<TmaRing<TV, NB> *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + TMA_WARPS * sizeof(TmaRing<TV, NB>));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        for (int b = 0; b < NB; ++b) mbar_init(&bars[NB * warp + b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncwarp();
+    const int gw = blockIdx.x * TMA_WARPS + warp;
+    const int c0 = __ldg(A.warp_chunk + gw), c1 = __ldg(A.warp_chunk + gw + 1);
+    bool timed_out = false;
+    const TX dot = spmv_warp_stream<TV, TX, NB>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
+    if (timed_out && lane == 0) atomicExch(&S->err, 1);
+    const double t = block_sum<NT>((double)dot, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (arrive_last(&S->ticket)) {
+        const double pq = sum_partials(partials, gridDim.x, 1, 0, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->pq = pq;
+            if (S->err) stop(S, ST_TIMEOUT);
+            else if (!(pq > 0.0) || !isfinite(pq)) stop(S, ST_BREAK);
+            else S->alpha = S->rho / pq;
+        }
+    }
+}
+
+template <class TV, class TX>
+static void launch_spmv_tma(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+                            PcgScal *S, cudaStream_t st) {
+    static bool attr_set = false;  // per instantiation
+    const int smem = (int)tma_smem_bytes<TV>();
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_spmv_tma<TV, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    ::gb::count_launches(1); k_spmv_tma<TV, TX><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+}
 
 // ------------------------------------------------------------ kernels --
 template <class TV, class TX, int C>
@@ -83,6 +137,12 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
     }
 }
 
+// Two elements per thread per step (16-byte loads for fp64, 8-byte for fp32);
+// n odd: the last element is handled by the thread that owns the last pair.
+template <class TX> struct Vec2;
+template <> struct Vec2<double> { using T = double2; };
+template <> struct Vec2<float> { using T = float2; };
+
 template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX *__restrict__ r,
                                                const TX *__restrict__ p, const TX *__restrict__ q,
@@ -90,15 +150,35 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
                                                PcgScal *S) {
     if (S->done) return;
     __shared__ double sm[NT / 32];
+    using V2 = typename Vec2<TX>::T;
+    using D2 = typename Vec2<TD>::T;
     const TX alpha = (TX)S->alpha;
     TX rz = TX(0), rr = TX(0);
-    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+    const int64_t npair = n >> 1;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < npair; i += (int64_t)gridDim.x * NT) {
+        V2 xv = reinterpret_cast<V2 *>(x)[i];
+        V2 rv = reinterpret_cast<V2 *>(r)[i];
+        const V2 pv = reinterpret_cast<const V2 *>(p)[i];
+        const V2 qv = reinterpret_cast<const V2 *>(q)[i];
+        const D2 dv = reinterpret_cast<const D2 *>(dinv)[i];
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        rv.x -= alpha * qv.x;
+        rv.y -= alpha * qv.y;
+        reinterpret_cast<V2 *>(x)[i] = xv;
+        reinterpret_cast<V2 *>(r)[i] = rv;
+        rz += rv.x * ((TX)dv.x * rv.x);
+        rz += rv.y * ((TX)dv.y * rv.y);
+        rr += rv.x * rv.x;
+        rr += rv.y * rv.y;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t i = n - 1;
         const TX xi = x[i] + alpha * p[i];
         const TX ri = r[i] - alpha * q[i];
-        const TX zi = (TX)dinv[i] * ri;
         x[i] = xi;
         r[i] = ri;
-        rz += ri * zi;
+        rz += ri * ((TX)dinv[i] * ri);
         rr += ri * ri;
     }
     const double a = block_sum<NT>((double)rz, sm);
@@ -129,9 +209,19 @@ template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, const TX *__restrict__ r,
                                                 const TD *__restrict__ dinv, const PcgScal *S) {
     if (S->done) return;
+    using V2 = typename Vec2<TX>::T;
+    using D2 = typename Vec2<TD>::T;
     const TX beta = (TX)S->beta;
-    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
-        p[i] = (TX)dinv[i] * r[i] + beta * p[i];
+    const int64_t npair = n >> 1;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < npair; i += (int64_t)gridDim.x * NT) {
+        V2 pv = reinterpret_cast<V2 *>(p)[i];
+        const V2 rv = reinterpret_cast<const V2 *>(r)[i];
+        const D2 dv = reinterpret_cast<const D2 *>(dinv)[i];
+        pv.x = (TX)dv.x * rv.x + beta * pv.x;
+        pv.y = (TX)dv.y * rv.y + beta * pv.y;
+        reinterpret_cast<V2 *>(p)[i] = pv;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = (TX)dinv[n - 1] * r[n - 1] + beta * p[n - 1];
 }
 
 // r = b - A x (fp64, x optional = 0) with ||r||^2 and ||b||^2.  The last block
@@ -208,6 +298,62 @@ __global__ void __launch_bounds__(NT) k_start(int64_t n, const TX *__restrict__ 
     }
 }
 
+// Residual replacement of a reliable update: r32 = (float) r64 from the fp64
+// true residual, and in fp64 sums rho' = r.D^-1 r, ||r||^2 and r.p.  The last
+// block prepares the step the stopped loop skipped, p = z + beta p, for the
+// replaced residual: beta = rho'/rho, with p first made orthogonal to the new
+// r along z (p -= (r.p / r.z) z), so p = (1 - beta c) z + beta p, c = r.p/rho'.
+// Re-arms the recurrence (done = 0).  first = 1: no previous p (k_start follows).
+__global__ void __launch_bounds__(NT) k_replace(int64_t n, const double *__restrict__ r64, const float *__restrict__ dinv,
+                                                float *__restrict__ r32, float *__restrict__ d32,
+                                                const float *__restrict__ p32, int first, double *partials, PcgScal *S) {
+    __shared__ double sm[NT / 32];
+    double rz = 0.0, rr = 0.0, rp = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+        const float ri = (float)r64[i];
+        r32[i] = ri;
+        d32[i] = 0.0f;
+        rz += (double)(ri * (dinv[i] * ri));
+        rr += (double)ri * (double)ri;
+        if (!first) rp += (double)ri * (double)p32[i];
+    }
+    const double a = block_sum<NT>(rz, sm);
+    const double b = block_sum<NT>(rr, sm);
+    const double c = block_sum<NT>(rp, sm);
+    if (threadIdx.x == 0) {
+        partials[3 * blockIdx.x] = a;
+        partials[3 * blockIdx.x + 1] = b;
+        partials[3 * blockIdx.x + 2] = c;
+    }
+    if (arrive_last(&S->ticket)) {
+        const double rz_t = sum_partials(partials, gridDim.x, 3, 0, sm);
+        const double rr_t = sum_partials(partials, gridDim.x, 3, 1, sm);
+        const double rp_t = sum_partials(partials, gridDim.x, 3, 2, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            if (!first && rz_t > 0.0 && S->rho > 0.0) {
+                const double beta = rz_t / S->rho;
+                S->beta = beta;
+                S->pz = 1.0 - beta * (rp_t / rz_t);
+            }
+            S->rho = rz_t;
+            S->rr = rr_t;
+            S->done = 0;
+            S->status = ST_RUN;
+            if (!(rz_t > 0.0)) { S->done = 1; S->status = rz_t == 0.0 ? ST_CONV : ST_BREAK; }
+        }
+    }
+}
+
+// p = pz D^-1 r + beta p (the restored direction of a reliable update)
+__global__ void __launch_bounds__(NT) k_replace_p(int64_t n, const float *__restrict__ r32, const float *__restrict__ dinv,
+                                                  float *__restrict__ p32, const PcgScal *S) {
+    if (S->done) return;
+    const float pz = (float)S->pz, beta = (float)S->beta;
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+        p32[i] = pz * (dinv[i] * r32[i]) + beta * p32[i];
+}
+
 __global__ void k_gather_d(int64_t n, const int32_t *perm, const double *src, double *dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = src ? src[perm[i]] : 0.0;
@@ -244,8 +390,10 @@ static Grids pick_grids(int64_t n, int C) {
 
 template <class TV, class TX, class TD>
 static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
-                              TX *q, double *partials, PcgScal *S, const Grids &g, cudaStream_t st) {
-    switch (A.C) {
+                              TX *q, double *partials, PcgScal *S, const Grids &g, cudaStream_t st,
+                              int variant = 0) {
+    if (variant == 0 && A.C == 32 && A.warp_chunk) launch_spmv_tma<TV, TX>(A, val, p, q, partials, S, st);
+    else switch (A.C) {
     case 32: ::gb::count_launches(1); k_spmv_pq<TV, TX, 32><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     case 64: ::gb::count_launches(1); k_spmv_pq<TV, TX, 64><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     default: ::gb::count_launches(1); k_spmv_pq<TV, TX, 128><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
@@ -332,6 +480,13 @@ static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &
     }
 }
 
+// partial-sum slots every solver kernel may write (2 per block of the largest grid)
+static size_t partial_slots(const gb_sell *A, const Grids &g) {
+    int blocks = std::max(g.spmv, g.vec);
+    if (A->warp_chunk) blocks = std::max(blocks, A->nwarps / TMA_WARPS);
+    return 3 * (size_t)blocks;
+}
+
 static PcgOptions defaults(const PcgOptions *o, int64_t n) {
     PcgOptions d{};
     if (o) d = *o;
@@ -360,6 +515,7 @@ static int init_scal(PcgScal *dS, long long maxit, cudaStream_t st) {
 static int map_status(int st) {
     switch (st) {
     case ST_CONV: return GB_OK;
+    case ST_TIMEOUT: return GB_TIMEOUT;
     case ST_BREAK: return GB_BREAKDOWN;
     case ST_MAXIT: return GB_NOT_CONVERGED;
     default: return GB_NOT_CONVERGED;
@@ -410,7 +566,8 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
         ++launches;
         GB_CHECK_CUDA(cudaGetLastError());
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.partials, w.S, g, s);
+            enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.partials, w.S, g, s,
+                                                      o.spmv_variant);
         };
         GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr));
         GB_TRY(read_scal(w.S, &h, st));
@@ -482,7 +639,8 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
         launches += 2;
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s);
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
+                                                o.spmv_variant);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
         PcgScal hi{};
@@ -511,6 +669,106 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
     return GB_OK;
 }
 
+// Reliable updates (Sleijpen & van der Vorst's residual replacement, in the
+// mixed-precision form used for lattice solvers): one fp32 CG recurrence on
+// the correction d runs until its recursive residual has dropped by a factor
+// RU_DELTA since the last replacement; then x += d and r = b - A x in fp64,
+// the convergence test in fp64, and the fp32 residual is replaced by the true
+// one while the search direction p is kept, so the Krylov information is not
+// thrown away as in restarted refinement.
+template <class TV>
+static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Work &w, cudaStream_t st,
+                    PcgStats *stats) {
+    constexpr double RU_DELTA = 0.1;
+    const SellView V = A->view();
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    Mem &mem = w.mem;
+    GB_TRY(mem.alloc_n(&w.r32, n));
+    GB_TRY(mem.alloc_n(&w.d32, n));
+    GB_TRY(mem.alloc_n(&w.p32, n));
+    GB_TRY(mem.alloc_n(&w.q32, n));
+    GB_TRY(mem.alloc_n(&w.S2, 1));
+    int64_t launches = 0;
+    enqueue_residual(V, o.x0_zero ? nullptr : w.x, w.b, w.r, w.partials, w.S, 1, o.tol, g, st);
+    ++launches;
+    PcgScal h{};
+    GB_TRY(read_scal(w.S, &h, st));
+    stats->bnorm = std::sqrt(h.bb);
+    if (h.bb == 0.0) {
+        GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
+        stats->relres = 0.0;
+        stats->status = GB_OK;
+        return GB_OK;
+    }
+    double rel = std::sqrt(h.rr / h.bb);
+    const double target2 = 0.25 * o.tol * o.tol * h.bb;  // fp32 recursive residual goal before a final check
+    int64_t inner_total = 0;
+    int updates = 0, stalls = 0;
+    double prev = rel;
+    double bytes = 0.0;
+    const double sval = sizeof(TV);
+    bool first = true;
+    {
+        PcgScal hs{};
+        hs.maxit = o.max_iter;
+        GB_CHECK_CUDA(cudaMemcpyAsync(w.S2, &hs, sizeof(PcgScal), cudaMemcpyHostToDevice, st));
+    }
+    while (rel > o.tol && inner_total < o.max_iter && updates < 1000) {
+        // replace the fp32 residual by the fp64 one; start p on the first pass only
+        ::gb::count_launches(1); k_replace<<<g.vec, NT, 0, st>>>(n, w.r, A->dinv32, w.r32, w.d32, w.p32, first ? 1 : 0,
+                                                               w.partials, w.S2);
+        ++launches;
+        if (first) {
+            ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
+            first = false;
+        } else {
+            ::gb::count_launches(1); k_replace_p<<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.S2);
+        }
+        ++launches;
+        PcgScal hr{};
+        GB_TRY(read_scal(w.S2, &hr, st));
+        if (hr.done) break;  // r32 == 0 or not positive: nothing to iterate on
+        {
+            // run until ||r32||^2 <= max(delta^2 ||r32_0||^2, target)
+            const double th = std::max(RU_DELTA * RU_DELTA * hr.rr, target2);
+            GB_CHECK_CUDA(cudaMemcpyAsync(&w.S2->thresh, &th, sizeof(double), cudaMemcpyHostToDevice, st));
+            const long long mx = o.max_iter;
+            GB_CHECK_CUDA(cudaMemcpyAsync(&w.S2->maxit, &mx, sizeof(long long), cudaMemcpyHostToDevice, st));
+        }
+        const long long it0 = hr.it;
+        auto body = [&](cudaStream_t s) {
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
+                                                o.spmv_variant);
+        };
+        GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
+        PcgScal hi{};
+        GB_TRY(read_scal(w.S2, &hi, st));
+        const long long dit = hi.it - it0;
+        inner_total = hi.it;
+        launches += 3 * dit;
+        bytes += dit * ((double)A->nnz * (sval + 4.0) + 7.0 * n * 4.0);
+        // x += d ; r = b - A x (fp64)
+        ::gb::count_launches(1); k_correct<<<g.vec, NT, 0, st>>>(n, w.x, 1.0, w.d32);
+        enqueue_residual(V, w.x, w.b, w.r, w.partials, w.S, 0, o.tol, g, st);
+        launches += 2;
+        bytes += (double)A->nnz * 12.0 + 5.0 * n * 8.0;
+        GB_TRY(read_scal(w.S, &h, st));
+        rel = std::sqrt(h.rr / h.bb);
+        ++updates;
+        if (hi.status == ST_BREAK || hi.status == ST_MAXIT) break;
+        if (!(rel < 0.9 * prev)) { if (++stalls >= 3) break; } else stalls = 0;
+        prev = std::min(prev, rel);
+    }
+    stats->iterations = inner_total;
+    stats->outer = updates;
+    stats->relres = rel;
+    stats->status = rel <= o.tol ? GB_OK : GB_NOT_CONVERGED;
+    stats->kernel_launches = launches;
+    stats->bytes_moved = bytes;
+    return GB_OK;
+}
+
 extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
                          void *stream, PcgStats *stats) {
     GB_REQUIRE(A && d_b && d_x, "pcg_solve: NULL argument");
@@ -518,9 +776,11 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     if (!stats) stats = &dummy;
     *stats = PcgStats{};
     PcgOptions o = defaults(opt, A->n);
-    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve: bad precision");
-    GB_REQUIRE(o.precision != GB_F32_IR || A->val32, "pcg_solve: F32_IR needs fp32 values (val_types)");
-    GB_REQUIRE(o.precision != GB_BF16_IR || A->val16, "pcg_solve: BF16_IR needs bf16 values (val_types)");
+    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_RU, "pcg_solve: bad precision");
+    GB_REQUIRE((o.precision != GB_F32_IR && o.precision != GB_F32_RU) || A->val32,
+               "pcg_solve: fp32-inner precisions need fp32 values (val_types)");
+    GB_REQUIRE((o.precision != GB_BF16_IR && o.precision != GB_BF16_RU) || A->val16,
+               "pcg_solve: bf16-inner precisions need bf16 values (val_types)");
     cudaStream_t st = (cudaStream_t)stream;
     Work w;
     w.mem = Mem(nullptr, st);
@@ -531,7 +791,7 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     GB_TRY(w.mem.alloc_n(&w.p, n));
     GB_TRY(w.mem.alloc_n(&w.q, n));
     GB_TRY(w.mem.alloc_n(&w.b, n));
-    GB_TRY(w.mem.alloc_n(&w.partials, 2 * (size_t)std::max(g.spmv, g.vec)));
+    GB_TRY(w.mem.alloc_n(&w.partials, partial_slots(A, g)));
     GB_TRY(w.mem.alloc_n(&w.S, 1));
     GB_TRY(init_scal(w.S, o.max_iter, st));
     cudaEvent_t e0, e1;
@@ -543,7 +803,9 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     int rc;
     if (o.precision == GB_F64) rc = solve_f64(A, o, w, st, stats);
     else if (o.precision == GB_F32_IR) rc = solve_ir<float>(A, A->val32, o, w, st, stats);
-    else rc = solve_ir<__nv_bfloat16>(A, A->val16, o, w, st, stats);
+    else if (o.precision == GB_BF16_IR) rc = solve_ir<__nv_bfloat16>(A, A->val16, o, w, st, stats);
+    else if (o.precision == GB_F32_RU) rc = solve_ru<float>(A, A->val32, o, w, st, stats);
+    else rc = solve_ru<__nv_bfloat16>(A, A->val16, o, w, st, stats);
     if (rc == GB_OK && o.precision != GB_F64 && stats->status != GB_OK && stats->iterations < o.max_iter) {
         // refinement stalled above tol: finish in fp64 from the current x
         PcgOptions o2 = o;
@@ -604,7 +866,7 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
     GB_TRY(w.mem.alloc_n(&w.d32, n));
     GB_TRY(w.mem.alloc_n(&w.p32, n));
     GB_TRY(w.mem.alloc_n(&w.q32, n));
-    GB_TRY(w.mem.alloc_n(&w.partials, 2 * (size_t)std::max(g.spmv, g.vec)));
+    GB_TRY(w.mem.alloc_n(&w.partials, partial_slots(A, g)));
     GB_TRY(w.mem.alloc_n(&w.S, 1));
     PcgScal hs{};
     hs.maxit = (long long)iters + 1;
@@ -626,7 +888,11 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
     cudaEventRecord(ev[0], st);
     for (int i = 0; i < iters; ++i) {
         for (int k = 0; k < 3; ++k) {
-            if (precision == GB_F64) {
+            if (k == 0 && A->C == 32 && A->warp_chunk) {
+                if (precision == GB_F64) launch_spmv_tma<double, double>(V, A->val, w.p, w.q, w.partials, w.S, st);
+                else if (precision == GB_F32_IR) launch_spmv_tma<float, float>(V, A->val32, w.p32, w.q32, w.partials, w.S, st);
+                else launch_spmv_tma<__nv_bfloat16, float>(V, A->val16, w.p32, w.q32, w.partials, w.S, st);
+            } else if (precision == GB_F64) {
                 if (k == 0) {
                     switch (A->C) {
                     case 32: ::gb::count_launches(1); k_spmv_pq<double, double, 32><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
@@ -695,7 +961,7 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
 // kernels, copies the few solver scalars back to the host and synchronises.
 namespace gb {
 constexpr int64_t NOALLOC_MAX_N = 262144;  // rows
-constexpr int64_t NOALLOC_PARTIALS = 4096;  // doubles: 2 per block, up to 256 SMs x 8 blocks
+constexpr int64_t NOALLOC_PARTIALS = 6144;  // doubles: 3 per block, up to 256 SMs x 8 blocks
 constexpr size_t NOALLOC_BYTES = (size_t)5 * NOALLOC_MAX_N * sizeof(double) +
                                  NOALLOC_PARTIALS * sizeof(double) + 256;
 // Every GPU that loads this library holds this array until the process exits.
@@ -741,9 +1007,9 @@ extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_
     o.use_graph = 0;  // graph objects would allocate: the loop is polled direct launches
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);
-    if (2 * (int64_t)std::max(g.spmv, g.vec) > NOALLOC_PARTIALS) {
-        set_error("pcg_solve_noalloc: this device needs %d partial sums, above the fixed %lld",
-                  2 * std::max(g.spmv, g.vec), (long long)NOALLOC_PARTIALS);
+    if ((int64_t)partial_slots(A, g) > NOALLOC_PARTIALS) {
+        set_error("pcg_solve_noalloc: this device needs %lld partial sums, above the fixed %lld",
+                  (long long)partial_slots(A, g), (long long)NOALLOC_PARTIALS);
         return GB_TOO_LARGE;
     }
     unsigned char *base = nullptr;

@@ -18,13 +18,15 @@ struct PcgScal {
     double rr;      // ||r||^2 (recursive)
     double bb;      // ||b||^2
     double thresh;  // tol^2 ||b||^2
+    double pz;      // reliable update: coefficient of z in the restored p
     long long it, maxit;
     int done, status;
     unsigned int ticket;  // last-block counter
+    int err;              // set by a kernel whose bounded wait ran out
     int use_cond;
     cudaGraphConditionalHandle cond;
 };
-enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3 };
+enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3, ST_TIMEOUT = 4 };
 
 // Streaming loads for the matrix (read once per iteration: evict first).
 __device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }

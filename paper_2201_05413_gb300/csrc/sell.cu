@@ -119,6 +119,22 @@ __global__ void k_sell_fill(int64_t n, int64_t nchunks, int C, const int32_t *pe
     }
 }
 
+// Warp w of the TMA SpMV owns chunks [warp_chunk[w], warp_chunk[w+1]): the
+// first chunk whose start is at or after w/nw of the padded nonzeros.
+__global__ void k_warp_partition(int64_t nchunks, const int64_t *chunk_ptr, int64_t padded, int nw,
+                                 int32_t *warp_chunk) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w <= nw; w += (int64_t)gridDim.x * blockDim.x) {
+        if (w == nw) { warp_chunk[w] = (int32_t)nchunks; continue; }
+        const int64_t target = (padded * w) / nw;
+        int64_t lo = 0, hi = nchunks;  // first c in [0, nchunks] with chunk_ptr[c] >= target
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (chunk_ptr[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        warp_chunk[w] = (int32_t)lo;
+    }
+}
+
 static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const double *v,
                       const double *diag_in, int max_row_hint, int C, int sigma, int val_types,
                       const gb_allocator *alloc, cudaStream_t st, gb_sell **out) {
@@ -198,6 +214,13 @@ static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const dou
         n, A->nchunks, C, A->perm, A->iperm, rp, ci, v, A->chunk_ptr, A->chunk_w, A->col, A->val,
         A->val32, A->val16);
     STEPC(cudaGetLastError());
+    if (C == 32) {  // chunk ranges of the TMA-staged SpMV (one per warp of its fixed grid)
+        A->nwarps = num_sms() * TMA_BLOCKS_PER_SM * 8;
+        STEP(mem.alloc_n(&A->warp_chunk, (size_t)A->nwarps + 1));
+        ::gb::count_launches(1); k_warp_partition<<<stride_grid(A->nwarps + 1, 256, 4), 256, 0, st>>>(
+            A->nchunks, A->chunk_ptr, padded, A->nwarps, A->warp_chunk);
+        STEPC(cudaGetLastError());
+    }
     STEPC(cudaStreamSynchronize(st));
     A->nnz = nnz32;
     mem.release(len);
@@ -306,7 +329,7 @@ extern "C" void sell_destroy(gb_sell *A) {
     Mem &m = A->mem;
     m.release(A->perm); m.release(A->iperm); m.release(A->row_len);
     m.release(A->dinv); m.release(A->dinv32);
-    m.release(A->chunk_w); m.release(A->chunk_ptr);
+    m.release(A->chunk_w); m.release(A->chunk_ptr); m.release(A->warp_chunk);
     m.release(A->col); m.release(A->val); m.release(A->val32); m.release(A->val16);
     delete A;
 }

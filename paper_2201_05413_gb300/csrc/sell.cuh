@@ -18,6 +18,9 @@ struct SellView {
     const __nv_bfloat16 *val16;
     const double *dinv;
     const float *dinv32;
+    const int32_t *chunk_w;
+    const int32_t *warp_chunk;  // nwarps+1 chunk bounds, balanced by padded nonzeros (C == 32)
+    int nwarps;
 };
 
 }  // namespace gb
@@ -26,12 +29,15 @@ struct gb_sell {
     int64_t n = 0, nnz = 0, padded = 0, nchunks = 0;
     int C = 32, sigma = 1, max_row = 0;
     int32_t *perm = nullptr, *iperm = nullptr, *row_len = nullptr, *chunk_w = nullptr, *col = nullptr;
+    int32_t *warp_chunk = nullptr;
+    int nwarps = 0;
     int64_t *chunk_ptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
     float *val32 = nullptr, *dinv32 = nullptr;
     __nv_bfloat16 *val16 = nullptr;
     gb::Mem mem;
     gb::SellView view() const {
-        return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32};
+        return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32,
+                            chunk_w, warp_chunk, nwarps};
     }
 };

@@ -1,0 +1,210 @@
+// spmv_tma.cuh -- SELL-32 SpMV with TMA-staged matrix streams.
+//
+// Each warp owns a contiguous range of chunks, balanced by padded nonzeros
+// (gb_sell::warp_chunk).  Because chunks are stored back to back, the range's
+// column indices and values are two contiguous arrays; the warp streams them
+// in stages of SJ column-steps (SJ*32 entries): one lane issues two 1-D bulk
+// copies (cp.async.bulk, the TMA's non-tensor form) per stage into a ring of
+// NB shared-memory buffers, each completing on its own mbarrier, with NB
+// stages in flight.  While the copies land, the lanes gather p for the stage
+// they hold (SJ independent loads back to back) and accumulate.  Waits use a
+// suspend-time hint and are bounded by %globaltimer: a wait that runs out
+// sets S->err (-> GB_TIMEOUT) and the warp stops, after letting its copies
+// in flight land.
+#pragma once
+#include "pcg.cuh"
+
+namespace gb {
+
+#ifndef GB_TMA_SJ
+#define GB_TMA_SJ 8
+#endif
+#ifndef GB_TMA_HINT_NS
+#define GB_TMA_HINT_NS 0
+#endif
+#ifndef GB_TMA_NB64
+#define GB_TMA_NB64 2
+#endif
+#ifndef GB_TMA_NB32
+#define GB_TMA_NB32 3
+#endif
+constexpr int SJ = GB_TMA_SJ;  // column-steps per staged slice
+constexpr int TMA_WARPS = 8;   // warps per block (TMA_BLOCKS_PER_SM blocks per SM)
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// try_wait with a suspend-time hint: the thread sleeps (up to the hint) until
+// the phase completes instead of spinning on issue slots
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+#if GB_TMA_HINT_NS > 0
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(GB_TMA_HINT_NS)
+        : "memory");
+#else
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+#endif
+    return ok != 0;
+}
+// bounded wait; true when the phase completed
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 8; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ring depth (stages in flight per warp): fp64 stages are 3 KB, fp32 2 KB, bf16 1.5 KB
+template <class TV> struct TmaDepth { static constexpr int NB = sizeof(TV) == 8 ? GB_TMA_NB64 : GB_TMA_NB32; };
+
+template <class TV, int NB>
+struct TmaRing {
+    int32_t col[NB][SJ * 32];
+    TV val[NB][SJ * 32];
+};
+
+template <class TV>
+constexpr size_t tma_smem_bytes() {
+    return TMA_WARPS * sizeof(TmaRing<TV, TmaDepth<TV>::NB>) + TMA_WARPS * TmaDepth<TV>::NB * sizeof(uint64_t);
+}
+
+template <class TX> __device__ __forceinline__ TX ldg_vec(const TX *p) { return __ldg(p); }
+
+template <class TX, class TV>
+__device__ __forceinline__ TX to_tx(TV v) {
+    if constexpr (sizeof(TV) == 2) return (TX)__bfloat162float(v);
+    else return (TX)v;
+}
+
+// One warp's chunk range as a linear stream.  The range's indices and values
+// are contiguous (chunks are stored back to back), so the warp walks them in
+// stages of SJ column-steps (SJ*32 entries) through a ring of NB shared-memory
+// buffers, NB stages in flight, independently of where chunks begin or end.
+// Inside a stage the SJ gathers of p are issued first, then the products are
+// accumulated; a chunk ends when its column counter reaches the chunk width.
+// Returns the warp's partial p.q (per lane); *timed_out on a wait that ran out.
+template <class TV, class TX, int NB>
+__device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__restrict__ val,
+                                               const TX *__restrict__ p, TX *__restrict__ q,
+                                               int c0, int c1, TmaRing<TV, NB> &sm, uint64_t *bars,
+                                               bool *timed_out) {
+    const int lane = threadIdx.x & 31;
+    TX dot = TX(0);
+    if (c0 >= c1) return dot;
+    const int64_t e0 = __ldg(A.chunk_ptr + c0), e1 = __ldg(A.chunk_ptr + c1);
+    const int64_t nsteps = (e1 - e0) >> 5;
+    const int64_t nstages = (nsteps + SJ - 1) / SJ;
+    auto issue = [&](int64_t st) {
+        if (lane == 0) {
+            const int b = (int)(st % NB);
+            const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
+            const int64_t off = e0 + st * SJ * 32;
+            const uint32_t bc = (uint32_t)(sj * 32 * sizeof(int32_t));
+            const uint32_t bv = (uint32_t)(sj * 32 * sizeof(TV));
+            mbar_expect_tx(&bars[b], bc + bv);
+            bulk_g2s(sm.col[b], A.col + off, bc, &bars[b]);
+            bulk_g2s(sm.val[b], val + off, bv, &bars[b]);
+        }
+    };
+    for (int64_t st = 0; st < nstages && st < NB; ++st) issue(st);
+    // current chunk (skip empty ones: they own no steps, their rows get q = 0)
+    int c = c0, w = __ldg(A.chunk_w + c);
+    while (w == 0) {
+        const int64_t rr = (int64_t)c * 32 + lane;
+        if (rr < A.n) q[rr] = TX(0);
+        ++c;
+        w = c < c1 ? __ldg(A.chunk_w + c) : 1;
+    }
+    int64_t r = (int64_t)c * 32 + lane;
+    int L = r < A.n ? __ldg(A.row_len + r) : 0;
+    int j = 0;
+    TX acc = TX(0);
+    int64_t st_fail = -1;
+    for (int64_t st = 0; st < nstages; ++st) {
+        const int b = (int)(st % NB);
+        const uint32_t parity = (uint32_t)((st / NB) & 1);
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(&bars[b], parity);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) {
+            *timed_out = true;
+            st_fail = st;
+            break;
+        }
+        const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
+        TX pv[SJ];
+#pragma unroll
+        for (int jj = 0; jj < SJ; ++jj)
+            if (jj < sj) pv[jj] = __ldg(p + sm.col[b][jj * 32 + lane]);
+#pragma unroll
+        for (int jj = 0; jj < SJ; ++jj) {
+            if (jj < sj) {
+                if (j < L) acc += to_tx<TX>(sm.val[b][jj * 32 + lane]) * pv[jj];
+                if (++j == w) {  // chunk complete (warp-uniform)
+                    if (r < A.n) {
+                        q[r] = acc;
+                        dot += __ldg(p + r) * acc;
+                    }
+                    acc = TX(0);
+                    j = 0;
+                    ++c;
+                    w = c < c1 ? __ldg(A.chunk_w + c) : 1;
+                    while (w == 0) {
+                        const int64_t rr = (int64_t)c * 32 + lane;
+                        if (rr < A.n) q[rr] = TX(0);
+                        ++c;
+                        w = c < c1 ? __ldg(A.chunk_w + c) : 1;
+                    }
+                    r = (int64_t)c * 32 + lane;
+                    L = (c < c1 && r < A.n) ? __ldg(A.row_len + r) : 0;
+                }
+            }
+        }
+        __syncwarp();
+        fence_proxy_async();  // our reads of buffer b precede the next bulk write into it
+        if (st + NB < nstages) issue(st + NB);
+    }
+    if (st_fail >= 0 && lane == 0) {
+        // stages [st_fail, st_fail + NB) were issued and not consumed: let
+        // their copies land before the buffers go away (bounded waits)
+        for (int64_t s2 = st_fail; s2 < nstages && s2 < st_fail + NB; ++s2)
+            (void)mbar_wait(&bars[s2 % NB], (uint32_t)((s2 / NB) & 1));
+    }
+    __syncwarp();
+    return dot;
+}
+
+}  // namespace gb

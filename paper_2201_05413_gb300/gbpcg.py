@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgbpcg.so")
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA = 0, -1, -2, -3
 GB_NOT_CONVERGED, GB_BREAKDOWN, GB_TIMEOUT, GB_TOO_LARGE, GB_PENDING = -4, -5, -6, -7, 1
 GB_VAL_F64, GB_VAL_F32, GB_VAL_BF16 = 1, 2, 4
-GB_F64, GB_F32_IR, GB_BF16_IR = 0, 1, 2
+GB_F64, GB_F32_IR, GB_BF16_IR, GB_F32_RU, GB_BF16_RU = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "NOT_CONVERGED",
                 -5: "BREAKDOWN", -6: "TIMEOUT", -7: "TOO_LARGE", 1: "PENDING"}
 
@@ -61,7 +61,7 @@ class gb_sell_info(C.Structure):
 class PcgOptions(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("check_every", C.c_int32),
-                ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("reserved", C.c_int32)]
+                ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("spmv_variant", C.c_int32)]
 
 
 class PcgStats(C.Structure):

@@ -81,7 +81,7 @@ def test_exact_polynomial_reproduction(P, case):
     assert O.x_err(u.cpu().numpy(), x.cpu().numpy()) <= XERR
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f32ru", "bf16ru"])
 @pytest.mark.parametrize("case", [
     (2, 1, 64, 1, 1, 2, O.G_X2_Y2),
     (2, 2, 32, 1, 1, 2, O.G_X2_Y2),
@@ -89,7 +89,7 @@ def test_exact_polynomial_reproduction(P, case):
     (3, 2, 12, 0, 0, 0, O.G_X2_Y2_2Z2),
 ])
 def test_mixed_refinement_matches_oracle(P, case, prec):
-    p = P.GB_F32_IR if prec == "f32" else P.GB_BF16_IR
+    p = {"f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR, "f32ru": P.GB_F32_RU, "bf16ru": P.GB_BF16_RU}[prec]
     d, s, xd, xo, st, ito, relres = _solve_both(P, *case, precision=p)
     assert st["status"] == 0
     assert relres <= 1.5 * TOL
