@@ -229,6 +229,66 @@ int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_
                       double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                       PcgStats *stats);
 
+/* ------------------------------------------------------------- serving --
+ * A solve server with continuous batching.  Requests (mesh spec, k right-
+ * hand sides) are admitted as resident "slots" while max_slots and the device
+ * memory budget allow; every resident slot advances in the same launches (the
+ * batched kernels), arrivals are assembled on a side stream while the others
+ * iterate, and finished slots free their memory for the next ones.  Each
+ * request's arithmetic depends only on its own data: its result is the same
+ * alone and in a mix.  precision GB_F32_RU (fp32 recurrences with fp64
+ * reliable updates, test and solution) or GB_F64.  One server thread per
+ * server; submit/poll/stats are thread-safe. */
+typedef struct gb_server gb_server;
+
+typedef struct ServeOptions {
+    size_t mem_budget;       /* device bytes the admitted requests may hold */
+    int32_t max_slots;       /* requests resident at once (1..4096) */
+    int32_t precision;       /* GB_F32_RU or GB_F64 */
+    double tol;              /* Eq. (2) threshold (0 = 1e-10) */
+    int64_t max_iter;        /* iterations per column (0 = 10^6) */
+    int32_t iters_per_step;  /* CG iterations between scheduling points (0 = 200) */
+    int32_t device;          /* CUDA device, -1 = the current one */
+} ServeOptions;
+
+typedef struct ServeRequest {
+    gb_fem_spec spec;        /* the system (fem_assemble) */
+    int32_t k;               /* right-hand sides, 1..32 */
+    int32_t gid;             /* Dirichlet data id (fem_dirichlet) when h_gB is NULL */
+    const double *h_coef;    /* coefficients for gid 3/4 (k x ncoef); copied at submit */
+    const double *h_gB;      /* or boundary values, n_bnd x k row-major (valid until done) */
+    double *h_x;             /* result, n_free x k row-major in free-dof order (valid until done) */
+} ServeRequest;
+
+typedef struct ServeResult {
+    int32_t status;          /* GB_OK, GB_NOT_CONVERGED, GB_BREAKDOWN, GB_TOO_LARGE, ... */
+    int32_t k;
+    int64_t n;               /* free dofs */
+    int64_t iterations;      /* max over the request's columns */
+    int32_t updates;         /* reliable updates made (GB_F32_RU) */
+    int32_t reserved;
+    double relres;           /* max over columns of ||b - A x|| / ||b|| (fp64) */
+    double queue_ms;         /* submit -> admitted (assembled, on the device) */
+    double latency_ms;       /* submit -> result written to h_x */
+    double bytes;            /* device bytes the request held */
+} ServeResult;
+
+typedef struct ServeStats {
+    int64_t submitted, completed, rejected, pending, resident, steps;
+    double mem_in_use, mem_peak;  /* bytes */
+    int32_t max_resident, reserved;
+} ServeStats;
+
+int serve_create(const ServeOptions *opt, gb_server **out);
+/* Non-blocking: queues the request and returns its ticket (> 0). */
+int serve_submit(gb_server *srv, const ServeRequest *req, uint64_t *ticket);
+/* GB_PENDING while the request runs; then its final status with *out filled
+ * (once: the result is released by the call that returns it). */
+int serve_poll(gb_server *srv, uint64_t ticket, ServeResult *out);
+int serve_stats(gb_server *srv, ServeStats *out);
+/* Finishes resident work, fails queued requests, joins the thread. */
+void serve_destroy(gb_server *srv);
+
 /* pcg_solve_noalloc -- the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory: code running inside another
  * allocator's callbacks, in a process whose device memory belongs to a fixed

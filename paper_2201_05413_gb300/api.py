@@ -209,3 +209,87 @@ def pcg_solve_batched(mats, Bs, Xs=None, raise_on_fail=True, stream=None, **kw):
     if raise_on_fail:
         G.check(rc, "pcg_solve_batched")
     return Xs, [dict(s.as_dict(), rc=rc) for s in stats]
+
+
+class Server:
+    """serve_create / serve_submit / serve_poll: a continuous-batching solve
+    server.  Host result buffers (numpy, n_free x k) are kept here until the
+    request completes."""
+
+    def __init__(self, mem_budget=40 << 30, max_slots=64, precision=G.GB_F32_RU, tol=1e-10,
+                 max_iter=0, iters_per_step=0, device=-1):
+        import numpy as np  # noqa: F401
+        o = G.ServeOptions(int(mem_budget), max_slots, precision, tol, max_iter, iters_per_step, device)
+        h = C.c_void_p()
+        G.check(G.lib().serve_create(C.byref(o), C.byref(h)), "serve_create")
+        self.handle = h
+        self._live = {}
+
+    @staticmethod
+    def sizes(dim, degree, cells):
+        S = degree * cells + 1
+        return (S - 2) ** dim, S ** dim - (S - 2) ** dim  # n_free, n_bnd
+
+    def submit(self, dim, degree, cells, jitter=0, diag_mode=0, seed=0, k=1, gid=1, coef=None, gB=None):
+        import numpy as np
+        n_free, n_bnd = self.sizes(dim, degree, cells)
+        x = np.zeros((n_free, k))
+        keep = [x]
+        req = G.ServeRequest()
+        req.spec = G.gb_fem_spec(dim, degree, cells, jitter, diag_mode, 0, seed)
+        req.k, req.gid = k, gid
+        req.h_x = x.ctypes.data_as(C.POINTER(C.c_double))
+        if coef is not None:
+            c = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+            keep.append(c)
+            req.h_coef = c.ctypes.data_as(C.POINTER(C.c_double))
+        if gB is not None:
+            g = np.ascontiguousarray(gB, dtype=np.float64).reshape(n_bnd, k)
+            keep.append(g)
+            req.h_gB = g.ctypes.data_as(C.POINTER(C.c_double))
+        t = C.c_uint64()
+        G.check(G.lib().serve_submit(self.handle, C.byref(req), C.byref(t)), "serve_submit")
+        self._live[t.value] = keep
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (result dict, x)."""
+        r = G.ServeResult()
+        rc = G.lib().serve_poll(self.handle, ticket, C.byref(r))
+        if rc == G.GB_PENDING:
+            return None
+        if rc == G.GB_EINVAL and ticket not in self._live:
+            G.check(rc, "serve_poll")
+        keep = self._live.pop(ticket)
+        return r.as_dict(), keep[0]
+
+    def wait(self, tickets, timeout_s=600.0, sleep_s=0.001):
+        import time
+        out, left = {}, set(tickets)
+        t0 = time.time()
+        while left:
+            for t in list(left):
+                r = self.poll(t)
+                if r is not None:
+                    out[t] = r
+                    left.discard(t)
+            if left:
+                if time.time() - t0 > timeout_s:
+                    raise TimeoutError(f"{len(left)} requests still pending")
+                time.sleep(sleep_s)
+        return out
+
+    def stats(self):
+        st = G.ServeStats()
+        G.check(G.lib().serve_stats(self.handle, C.byref(st)), "serve_stats")
+        return st.as_dict()
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h and G._lib is not None:
+            G._lib.serve_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        if not sys.is_finalizing():
+            self.close()

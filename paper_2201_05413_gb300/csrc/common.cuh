@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <string>
 

@@ -1,0 +1,703 @@
+// serve.cu -- continuous-batching solve server (serve_create / submit / poll).
+//
+// A server thread owns two streams.  On the main stream it advances every
+// resident request ("slot": its matrix, right-hand sides and Krylov state stay
+// on the device) by a chunk of CG iterations in shared launches -- the batched
+// kernels of batched.cuh over a table of the iterating slots.  While a chunk
+// runs, pending requests are admitted on the side stream as slots and memory
+// allow: device assembly, SELL conversion, Dirichlet lift and the start of
+// their recurrences, allocated from a stream-ordered pool and charged against
+// the memory budget.  A chunk ends after iters_per_step iterations or as soon
+// as a slot's columns have all stopped; the thread then services those slots
+// (fp32 recurrences: the reliable update -- x += d and r = b - A x in fp64,
+// the fp64 test, residual replacement; fp64 recurrences: the true-residual
+// check), retires finished ones (x copied to the caller's host buffer, memory
+// freed), and rebuilds the table with the new arrivals.  A slot's arithmetic
+// depends only on its own data, so its result is the same alone and in a mix.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "batched.cuh"
+
+namespace gb {
+
+static bool log_on() {
+    static int v = -1;
+    if (v < 0) { const char *e = getenv("GBPCG_LOG"); v = (e && *e && *e != '0') ? 1 : 0; }
+    return v == 1;
+}
+
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct SReq {
+    uint64_t ticket;
+    ServeRequest r;
+    std::vector<double> coef;
+    double t_submit;
+};
+
+enum { SL_ITER = 0, SL_SERVICE = 1, SL_DONE = 2 };
+
+struct Slot {
+    SReq q;
+    gb_fem_system *sys = nullptr;
+    gb_sell *A = nullptr;
+    int64_t n = 0;
+    int k = 1, kw = 1;
+    bool ru = true;
+    double *B64 = nullptr, *X64 = nullptr, *R64 = nullptr;
+    void *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
+    double *cd = nullptr;
+    long long *ci = nullptr;
+    int *cs = nullptr;
+    ColState c{};
+    std::vector<void *> bufs;  // engine-owned device buffers of this slot
+    std::vector<int> fin;      // per column: 1 = final
+    std::vector<int> fstat;    // final status per column
+    std::vector<double> rel, best;
+    std::vector<int> stalls;
+    int updates = 0;
+    int state = SL_ITER;
+    int active = 0;            // columns iterating
+    double t_admit = 0.0;
+    size_t bytes = 0;
+    int units = 1;
+    int64_t rows_per_unit = 1;
+};
+
+}  // namespace gb
+
+struct gb_server {
+    ServeOptions opt{};
+    int dev = 0;
+    cudaStream_t main_st = nullptr, side_st = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<gb::SReq> inbox;
+    std::map<uint64_t, ServeResult> results;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    // accounting (server thread; read under mu for stats)
+    ServeStats stats{};
+    size_t in_use = 0, peak = 0;
+    size_t slot_bytes_acc = 0;  // bytes allocated while admitting the current slot
+    std::unordered_map<void *, size_t> sizes;
+    gb_allocator alloc{};
+    // table buffers (main stream)
+    gb::BSys *d_sys = nullptr;
+    int *d_unit_sys = nullptr, *d_mask = nullptr;
+    gb::BGlobal *d_G = nullptr;
+    double *d_partials = nullptr;
+    size_t cap_umap = 0, cap_part = 0;
+    // single-slot buffers used while admitting (side stream)
+    gb::BSys *d_sys1 = nullptr;
+    int *d_unit1 = nullptr, *d_mask1 = nullptr;
+    double *d_partials1 = nullptr;
+    size_t cap_umap1 = 0, cap_part1 = 0;
+    std::vector<std::unique_ptr<gb::Slot>> slots;
+    std::deque<gb::SReq> pending;
+    int fatal = GB_OK;
+    std::string fatal_msg;
+};
+
+using namespace gb;
+
+// ------------------------------------------------------------- allocator --
+// Stream-ordered pool allocations on the side stream, counted per slot.
+static void *srv_alloc(void *ctx, size_t bytes, void *stream) {
+    gb_server *s = (gb_server *)ctx;
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) return nullptr;
+    s->sizes[p] = bytes;
+    s->in_use += bytes;
+    s->slot_bytes_acc += bytes;
+    s->peak = std::max(s->peak, s->in_use);
+    return p;
+}
+static void srv_free(void *ctx, void *p, void *stream) {
+    gb_server *s = (gb_server *)ctx;
+    if (!p) return;
+    auto it = s->sizes.find(p);
+    if (it != s->sizes.end()) {
+        s->in_use -= it->second;
+        s->sizes.erase(it);
+    }
+    cudaFreeAsync(p, (cudaStream_t)stream);
+}
+
+template <class T>
+static int srv_take(gb_server *s, Slot &sl, T **p, size_t n) {
+    void *q = srv_alloc(s, std::max<size_t>(n * sizeof(T), 256), s->side_st);
+    if (!q) { set_error("serve: device allocation of %zu bytes failed", n * sizeof(T)); return GB_ENOMEM; }
+    sl.bufs.push_back(q);
+    *p = (T *)q;
+    return GB_OK;
+}
+
+static int units_of(int64_t n, int kw, int64_t *rows_per_unit) {
+    const int64_t groups = NT / kw;
+    int64_t units = (n + groups * 4 - 1) / (groups * 4);
+    units = std::max<int64_t>(1, std::min<int64_t>(units, 2048));
+    *rows_per_unit = (n + units - 1) / units;
+    return (int)((n + *rows_per_unit - 1) / *rows_per_unit);
+}
+
+static BSys desc_of(const Slot &sl, int unit0) {
+    BSys S{};
+    S.A = sl.A->view();
+    S.val = sl.ru ? (const void *)sl.A->val32 : (const void *)sl.A->val;
+    S.X = sl.X; S.R = sl.R; S.P = sl.P; S.Q = sl.Q;
+    S.B64 = sl.B64; S.X64 = sl.X64; S.R64 = sl.R64;
+    S.c = sl.c;
+    S.k = sl.k; S.kw = sl.kw;
+    S.unit0 = unit0;
+    S.nunits = sl.units;
+    S.rows_per_unit = sl.rows_per_unit;
+    S.ticket = 0;
+    S.active = sl.active;
+    return S;
+}
+
+// device bytes one request will hold (upper estimate from its spec)
+static size_t estimate_bytes(const ServeRequest &r, bool ru) {
+    const int64_t S = (int64_t)r.spec.degree * r.spec.cells + 1;
+    int64_t nd = 1, nf = 1;
+    for (int d = 0; d < r.spec.dim; ++d) { nd *= S; nf *= (S - 2); }
+    const double per_row = r.spec.dim == 2 ? (r.spec.degree == 1 ? 9.0 : 25.0) : (r.spec.degree == 1 ? 15.0 : 65.0);
+    const double nnz = per_row * nf;
+    const double nb = (double)(nd - nf);
+    double b = nnz * 12.0 * 1.05           // CSR
+               + nnz * 1.45 * (4 + 8 + (ru ? 4 : 0))  // SELL (padding bound)
+               + nf * 60.0                  // row pointers, maps, diag, dinv, perm
+               + nb * 16.0 + 4.0 * per_row * nb   // K_IB, boundary maps
+               + (double)nf * r.k * (ru ? (3 * 8 + 4 * 4) : 5 * 8)  // vectors
+               + (double)nb * r.k * 8 + (double)nf * r.k * 8     // lift temporaries
+               + 65536;
+    return (size_t)b;
+}
+
+static void finish(gb_server *s, const SReq &q, int status, const Slot *sl) {
+    ServeResult R{};
+    R.status = status;
+    R.k = q.r.k;
+    if (sl) {
+        R.n = sl->n;
+        R.updates = sl->updates;
+        R.bytes = (double)sl->bytes;
+        R.queue_ms = sl->t_admit - q.t_submit;
+    }
+    R.latency_ms = now_ms() - q.t_submit;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->results[q.ticket] = R;
+    if (status == GB_TOO_LARGE && !sl) s->stats.rejected += 1;
+    s->stats.completed += 1;
+}
+
+static void release_slot(gb_server *s, Slot &sl) {
+    for (void *p : sl.bufs) srv_free(s, p, s->side_st);
+    sl.bufs.clear();
+    if (sl.A) { sell_destroy(sl.A); sl.A = nullptr; }
+    if (sl.sys) { fem_system_destroy(sl.sys); sl.sys = nullptr; }
+}
+
+// grow a device buffer owned by the engine (not charged to any slot)
+template <class T>
+static int grow(gb_server *s, T **p, size_t *cap, size_t need, cudaStream_t st) {
+    if (*p && *cap >= need) return GB_OK;
+    if (*p) { cudaStreamSynchronize(st); cudaFree(*p); *p = nullptr; }
+    size_t c = std::max<size_t>(need, 1024);
+    GB_CHECK_CUDA(cudaMalloc((void **)p, c * sizeof(T)));
+    *cap = c;
+    return GB_OK;
+}
+
+// --------------------------------------------------------------- admit --
+static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
+    const bool ru = s->opt.precision != GB_F64;
+    auto sl = std::make_unique<Slot>();
+    Slot &L = *sl;
+    L.q = q;
+    L.ru = ru;
+    L.k = q.r.k;
+    L.kw = 1;
+    while (L.kw < L.k) L.kw <<= 1;
+    s->slot_bytes_acc = 0;
+    cudaStream_t st = s->side_st;
+    int rc = fem_assemble(&q.r.spec, &s->alloc, st, &L.sys);
+    if (rc == GB_OK) rc = csr_to_sell(L.sys, 32, 256, ru ? (GB_VAL_F64 | GB_VAL_F32) : GB_VAL_F64, &s->alloc, st, &L.A);
+    if (rc != GB_OK) { L.bytes = s->slot_bytes_acc; release_slot(s, L); return rc; }
+    gb_fem_info fi{};
+    fem_system_info(L.sys, &fi);
+    L.n = fi.n_free;
+    const size_t nk = (size_t)L.n * L.k;
+    double *gB = nullptr, *bfull = nullptr;
+    rc = srv_take(s, L, &L.B64, nk);
+    if (rc == GB_OK) rc = srv_take(s, L, &L.X64, nk);
+    if (rc == GB_OK) rc = srv_take(s, L, &L.R64, nk);
+    if (rc == GB_OK) rc = srv_take(s, L, &gB, (size_t)fi.n_bnd * L.k);
+    if (rc == GB_OK) rc = srv_take(s, L, &bfull, nk);
+    if (rc == GB_OK) {
+        if (ru) {
+            float *X, *R, *P, *Q;
+            rc = srv_take(s, L, &X, nk);
+            if (rc == GB_OK) rc = srv_take(s, L, &R, nk);
+            if (rc == GB_OK) rc = srv_take(s, L, &P, nk);
+            if (rc == GB_OK) rc = srv_take(s, L, &Q, nk);
+            L.X = X; L.R = R; L.P = P; L.Q = Q;
+        } else {
+            double *P, *Q;
+            rc = srv_take(s, L, &P, nk);
+            if (rc == GB_OK) rc = srv_take(s, L, &Q, nk);
+            L.X = L.X64; L.R = L.R64; L.P = P; L.Q = Q;
+        }
+    }
+    if (rc == GB_OK) rc = srv_take(s, L, &L.cd, (size_t)10 * KMAX);
+    if (rc == GB_OK) rc = srv_take(s, L, &L.ci, (size_t)KMAX);
+    if (rc == GB_OK) rc = srv_take(s, L, &L.cs, (size_t)2 * KMAX);
+    if (rc != GB_OK) { L.bytes = s->slot_bytes_acc; release_slot(s, L); return rc; }
+    L.c.rho = L.cd; L.c.pq = L.cd + KMAX; L.c.alpha = L.cd + 2 * KMAX; L.c.beta = L.cd + 3 * KMAX;
+    L.c.rr = L.cd + 4 * KMAX; L.c.bb = L.cd + 5 * KMAX; L.c.thresh = L.cd + 6 * KMAX; L.c.scale = L.cd + 7 * KMAX;
+    L.c.pz = L.cd + 8 * KMAX; L.c.target = L.cd + 9 * KMAX;
+    L.c.it = L.ci;
+    L.c.done = L.cs; L.c.status = L.cs + KMAX;
+    auto fail = [&](const char *what, cudaError_t e) {
+        set_error("serve admit: %s: %s", what, cudaGetErrorString(e));
+        L.bytes = s->slot_bytes_acc;
+        release_slot(s, L);
+        return GB_ECUDA;
+    };
+    cudaError_t e = cudaMemsetAsync(L.cd, 0, sizeof(double) * 10 * KMAX, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.ci, 0, sizeof(long long) * KMAX, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.cs, 0, sizeof(int) * 2 * KMAX, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.X64, 0, sizeof(double) * nk, st);
+    if (e != cudaSuccess) return fail("memset", e);
+    // right-hand sides: b = -K_IB g_B in free-dof order, then permuted
+    if (q.r.h_gB) {
+        e = cudaMemcpyAsync(gB, q.r.h_gB, sizeof(double) * fi.n_bnd * L.k, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail("gB copy", e);
+    } else {
+        rc = fem_dirichlet(L.sys, q.r.gid, q.coef.empty() ? nullptr : q.coef.data(), L.k, 0, gB, st);
+        if (rc != GB_OK) { L.bytes = s->slot_bytes_acc; release_slot(s, L); return rc; }
+    }
+    rc = fem_lift_rhs(L.sys, gB, L.k, bfull, st);
+    if (rc != GB_OK) { L.bytes = s->slot_bytes_acc; release_slot(s, L); return rc; }
+    ::gb::count_launches(1);
+    k_gather_rows<<<stride_grid((int64_t)nk, 256, 8), 256, 0, st>>>(L.n, L.k, L.A->perm, bfull, L.B64);
+    // single-slot table: initial residual (x0 = 0), norms, thresholds
+    L.units = units_of(L.n, L.kw, &L.rows_per_unit);
+    GB_TRY(grow(s, &s->d_partials1, &s->cap_part1, (size_t)L.units * 3 * KMAX, st));
+    std::vector<int> umap(L.units, 0);
+    GB_TRY(grow(s, &s->d_unit1, &s->cap_umap1, (size_t)L.units, st));
+    L.active = 0;
+    BSys d1 = desc_of(L, 0);
+    e = cudaMemcpyAsync(s->d_sys1, &d1, sizeof(BSys), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_unit1, umap.data(), sizeof(int) * L.units, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail("table", e);
+    ::gb::count_launches(1);
+    k_bresid<<<L.units, NT, 0, st>>>(s->d_sys1, s->d_unit1, s->d_partials1, 1, 1, s->opt.tol);
+    std::vector<double> bb(L.k), rr(L.k);
+    e = cudaMemcpyAsync(bb.data(), L.c.bb, sizeof(double) * L.k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail("init residual", e);
+    srv_free(s, gB, st);
+    srv_free(s, bfull, st);
+    L.bufs.erase(std::remove(L.bufs.begin(), L.bufs.end(), (void *)gB), L.bufs.end());
+    L.bufs.erase(std::remove(L.bufs.begin(), L.bufs.end(), (void *)bfull), L.bufs.end());
+    L.fin.assign(L.k, 0);
+    L.fstat.assign(L.k, GB_OK);
+    L.rel.assign(L.k, 1.0);
+    L.best.assign(L.k, 1.0);
+    L.stalls.assign(L.k, 0);
+    std::vector<int> mask(KMAX, 0);
+    std::vector<double> target(KMAX, 0.0);
+    for (int j = 0; j < L.k; ++j) {
+        if (bb[j] == 0.0) { L.fin[j] = 1; L.rel[j] = 0.0; continue; }  // zero data: x = 0
+        mask[j] = ru ? 2 : 1;
+        target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
+    }
+    e = cudaMemcpyAsync(s->d_mask1, mask.data(), sizeof(int) * KMAX, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.c.target, target.data(), sizeof(double) * KMAX, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail("mask", e);
+    if (ru) {
+        ::gb::count_launches(2);
+        k_breplace<<<L.units, NT, 0, st>>>(s->d_sys1, s->d_unit1, s->d_partials1, s->d_mask1, 0.01);
+        k_breplace_p<<<L.units, NT, 0, st>>>(s->d_sys1, s->d_unit1, s->d_mask1);
+    } else {
+        ::gb::count_launches(1);
+        k_bstart<double><<<L.units, NT, 0, st>>>(s->d_sys1, s->d_unit1, s->d_partials1, s->d_mask1);
+    }
+    std::vector<int> done(L.k);
+    e = cudaMemcpyAsync(done.data(), L.c.done, sizeof(int) * L.k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail("start", e);
+    for (int j = 0; j < L.k; ++j) L.active += (!L.fin[j] && !done[j]) ? 1 : 0;
+    L.state = L.active ? SL_ITER : SL_SERVICE;
+    L.bytes = s->slot_bytes_acc;
+    L.t_admit = now_ms();
+    out = std::move(sl);
+    return GB_OK;
+}
+
+// --------------------------------------------------------- retire / service --
+static void retire(gb_server *s, Slot &L, int status) {
+    // x back in free-dof order into the caller's buffer
+    double *xo = nullptr;
+    int rc = srv_take(s, L, &xo, (size_t)L.n * L.k);
+    cudaError_t e = cudaSuccess;
+    if (rc == GB_OK) {
+        ::gb::count_launches(1);
+        k_scatter_rows<<<stride_grid(L.n * L.k, 256, 8), 256, 0, s->side_st>>>(L.n, L.k, L.A->perm, L.X64, xo);
+        e = cudaMemcpyAsync(L.q.r.h_x, xo, sizeof(double) * L.n * L.k, cudaMemcpyDeviceToHost, s->side_st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->side_st);
+    }
+    if (rc != GB_OK || e != cudaSuccess) status = rc != GB_OK ? rc : GB_ECUDA;
+    std::vector<long long> it(L.k, 0);
+    cudaMemcpy(it.data(), L.c.it, sizeof(long long) * L.k, cudaMemcpyDeviceToHost);
+    release_slot(s, L);
+    ServeResult R{};
+    R.status = status;
+    R.k = L.k;
+    R.n = L.n;
+    for (int j = 0; j < L.k; ++j) {
+        R.iterations = std::max<int64_t>(R.iterations, it[j]);
+        R.relres = std::max(R.relres, L.rel[j]);
+    }
+    R.updates = L.updates;
+    R.bytes = (double)L.bytes;
+    R.queue_ms = L.t_admit - L.q.t_submit;
+    R.latency_ms = now_ms() - L.q.t_submit;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->results[L.q.ticket] = R;
+    s->stats.completed += 1;
+    s->stats.resident -= 1;
+    L.state = SL_DONE;
+}
+
+// Slots whose columns have all stopped: fp64 correction and residual, the
+// fp64 test per column, then either final or re-armed (replacement / restart).
+static int service(gb_server *s, std::vector<Slot *> &sv) {
+    if (sv.empty()) return GB_OK;
+    cudaStream_t st = s->main_st;
+    const bool ru = s->opt.precision != GB_F64;
+    std::vector<BSys> tab;
+    std::vector<int> umap;
+    for (size_t i = 0; i < sv.size(); ++i) {
+        tab.push_back(desc_of(*sv[i], (int)umap.size()));
+        for (int u = 0; u < sv[i]->units; ++u) umap.push_back((int)i);
+    }
+    GB_TRY(grow(s, &s->d_partials, &s->cap_part, umap.size() * 3 * KMAX, st));
+    GB_TRY(grow(s, &s->d_unit_sys, &s->cap_umap, umap.size(), st));
+    std::vector<int> mask(tab.size() * KMAX, 0);
+    for (size_t i = 0; i < sv.size(); ++i)
+        for (int j = 0; j < sv[i]->k; ++j) mask[i * KMAX + j] = sv[i]->fin[j] ? 0 : 1;
+    GB_CHECK_CUDA(cudaMemcpyAsync(s->d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(s->d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(s->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
+    const int U = (int)umap.size();
+    if (ru) {
+        // scale = 1: X64 += D for the columns that were iterating
+        for (auto *L : sv) {
+            std::vector<double> one(KMAX, 1.0);
+            GB_CHECK_CUDA(cudaMemcpyAsync(L->c.scale, one.data(), sizeof(double) * KMAX, cudaMemcpyHostToDevice, st));
+        }
+        ::gb::count_launches(1);
+        k_bcorrect<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_mask);
+    }
+    ::gb::count_launches(1);
+    k_bresid<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, 0, 0, s->opt.tol);
+    GB_CHECK_CUDA(cudaGetLastError());
+    // decide per column
+    bool any = false;
+    for (size_t i = 0; i < sv.size(); ++i) {
+        Slot &L = *sv[i];
+        std::vector<double> rr(L.k), bb(L.k);
+        std::vector<int> stat(L.k);
+        std::vector<long long> it(L.k);
+        GB_CHECK_CUDA(cudaMemcpyAsync(rr.data(), L.c.rr, sizeof(double) * L.k, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaMemcpyAsync(bb.data(), L.c.bb, sizeof(double) * L.k, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaMemcpyAsync(stat.data(), L.c.status, sizeof(int) * L.k, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaMemcpyAsync(it.data(), L.c.it, sizeof(long long) * L.k, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));
+        L.updates += ru ? 1 : 0;
+        for (int j = 0; j < L.k; ++j) {
+            const int m = mask[i * KMAX + j];
+            if (!m) continue;
+            const double rel = bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0;
+            L.rel[j] = rel;
+            int nm = 0;
+            if (rel <= s->opt.tol) { L.fin[j] = 1; L.fstat[j] = GB_OK; }
+            else if (stat[j] == ST_MAXIT || it[j] >= s->opt.max_iter) { L.fin[j] = 1; L.fstat[j] = GB_NOT_CONVERGED; }
+            else {
+                if (rel < 0.9 * L.best[j]) { L.best[j] = rel; L.stalls[j] = 0; }
+                else if (++L.stalls[j] >= 4) { L.fin[j] = 1; L.fstat[j] = GB_NOT_CONVERGED; }
+                if (!L.fin[j]) nm = (stat[j] == ST_BREAK) ? 2 : 1;  // breakdown: fresh direction
+            }
+            mask[i * KMAX + j] = nm;
+            any |= nm != 0;
+            if (log_on())
+                fprintf(stderr, "[gbpcg serve] ticket %llu col %d: it %lld status %d rel %.3e best %.3e stalls %d -> %s\n",
+                        (unsigned long long)L.q.ticket, j, it[j], stat[j], rel, L.best[j], L.stalls[j],
+                        L.fin[j] ? (L.fstat[j] == GB_OK ? "converged" : "stopped") : (nm == 2 ? "fresh start" : "replace"));
+        }
+    }
+    if (any) {
+        GB_CHECK_CUDA(cudaMemcpyAsync(s->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
+        if (ru) {
+            ::gb::count_launches(2);
+            k_breplace<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, s->d_mask, 0.01);
+            k_breplace_p<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_mask);
+        } else {
+            // fp64 recurrence: restart from the true residual (R64 already holds it)
+            ::gb::count_launches(1);
+            k_bstart<double><<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, s->d_mask);
+        }
+        GB_CHECK_CUDA(cudaGetLastError());
+    }
+    for (size_t i = 0; i < sv.size(); ++i) {
+        Slot &L = *sv[i];
+        std::vector<int> done(L.k);
+        GB_CHECK_CUDA(cudaMemcpyAsync(done.data(), L.c.done, sizeof(int) * L.k, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));
+        L.active = 0;
+        bool all_final = true;
+        for (int j = 0; j < L.k; ++j) {
+            if (!L.fin[j] && mask[i * KMAX + j] && done[j]) {  // re-arming found nothing to do
+                L.fin[j] = 1;
+                L.fstat[j] = L.rel[j] <= s->opt.tol ? GB_OK : GB_BREAKDOWN;
+            }
+            if (!L.fin[j]) { all_final = false; L.active += done[j] ? 0 : 1; }
+        }
+        if (all_final) {
+            int st2 = GB_OK;
+            for (int j = 0; j < L.k; ++j) if (L.fstat[j] != GB_OK) st2 = L.fstat[j];
+            retire(s, L, st2);
+        } else {
+            L.state = L.active ? SL_ITER : SL_SERVICE;
+        }
+    }
+    return GB_OK;
+}
+
+// ---------------------------------------------------------------- loop --
+static void server_loop(gb_server *s) {
+    cudaSetDevice(s->dev);
+    const bool ru = s->opt.precision != GB_F64;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            while (!s->inbox.empty()) { s->pending.push_back(std::move(s->inbox.front())); s->inbox.pop_front(); }
+            if (s->stopping && s->pending.empty() && s->slots.empty()) break;
+            if (s->pending.empty() && s->slots.empty()) {
+                s->cv.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+        }
+        // A. launch a chunk of CG iterations for the iterating slots (main stream)
+        std::vector<Slot *> it_slots;
+        for (auto &p : s->slots) if (p->state == SL_ITER) it_slots.push_back(p.get());
+        bool launched = false;
+        if (!it_slots.empty()) {
+            std::vector<BSys> tab;
+            std::vector<int> umap;
+            for (size_t i = 0; i < it_slots.size(); ++i) {
+                tab.push_back(desc_of(*it_slots[i], (int)umap.size()));
+                for (int u = 0; u < it_slots[i]->units; ++u) umap.push_back((int)i);
+            }
+            int rc = grow(s, &s->d_unit_sys, &s->cap_umap, umap.size(), s->main_st);
+            if (rc == GB_OK) rc = grow(s, &s->d_partials, &s->cap_part, umap.size() * 3 * KMAX, s->main_st);
+            BGlobal g{};
+            g.maxit = s->opt.max_iter;
+            g.active_systems = (int)it_slots.size();
+            g.stop_on_retire = 1;
+            g.budget = s->opt.iters_per_step;
+            cudaError_t e = cudaMemcpyAsync(s->d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, s->main_st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, s->main_st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_G, &g, sizeof(g), cudaMemcpyHostToDevice, s->main_st);
+            const int U = (int)umap.size();
+            for (int i = 0; i < s->opt.iters_per_step && e == cudaSuccess && rc == GB_OK; ++i) {
+                ::gb::count_launches(3);
+                if (ru) {
+                    k_bspmm<float, float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    k_bupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    k_bpupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
+                } else {
+                    k_bspmm<double, double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    k_bupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    k_bpupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
+                }
+            }
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->main_st);
+            if (e != cudaSuccess || rc != GB_OK) {
+                s->fatal = e != cudaSuccess ? GB_ECUDA : rc;
+                s->fatal_msg = e != cudaSuccess ? cudaGetErrorString(e) : gbpcg_last_error();
+                break;
+            }
+            launched = true;
+            s->stats.steps += 1;
+        }
+        // B. admit while the chunk runs (side stream)
+        while (!s->pending.empty() && (int)s->slots.size() < s->opt.max_slots) {
+            SReq &q = s->pending.front();
+            const size_t est = estimate_bytes(q.r, ru);
+            if (est > s->opt.mem_budget) {
+                set_error("request %llu needs ~%zu bytes, above the budget", (unsigned long long)q.ticket, est);
+                finish(s, q, GB_TOO_LARGE, nullptr);
+                s->pending.pop_front();
+                continue;
+            }
+            if (s->in_use + est > s->opt.mem_budget) break;  // wait for memory
+            std::unique_ptr<Slot> sl;
+            const int rc = admit(s, q, sl);
+            if (rc != GB_OK) {
+                finish(s, q, rc, nullptr);
+                s->pending.pop_front();
+                continue;
+            }
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->stats.resident += 1;
+                s->stats.max_resident = std::max<int32_t>(s->stats.max_resident, (int32_t)s->stats.resident);
+            }
+            s->slots.push_back(std::move(sl));
+            s->pending.pop_front();
+        }
+        // C. wait for the chunk, pull the column states of the slots in it
+        if (launched) {
+            cudaError_t e = cudaEventSynchronize(s->ev);
+            for (Slot *L : it_slots) {
+                if (e != cudaSuccess) break;
+                std::vector<int> done(L->k);
+                e = cudaMemcpy(done.data(), L->c.done, sizeof(int) * L->k, cudaMemcpyDeviceToHost);
+                int a = 0;
+                for (int j = 0; j < L->k; ++j) a += (!L->fin[j] && !done[j]) ? 1 : 0;
+                L->active = a;
+                if (a == 0) L->state = SL_SERVICE;
+            }
+            if (e != cudaSuccess) { s->fatal = GB_ECUDA; s->fatal_msg = cudaGetErrorString(e); break; }
+        }
+        // D. service slots whose columns all stopped; E. drop retired slots
+        std::vector<Slot *> sv;
+        for (auto &p : s->slots) if (p->state == SL_SERVICE) sv.push_back(p.get());
+        const int rc = service(s, sv);
+        if (rc != GB_OK) { s->fatal = rc; s->fatal_msg = gbpcg_last_error(); break; }
+        s->slots.erase(std::remove_if(s->slots.begin(), s->slots.end(),
+                                      [](const std::unique_ptr<Slot> &p) { return p->state == SL_DONE; }),
+                       s->slots.end());
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stats.mem_in_use = (double)s->in_use;
+            s->stats.mem_peak = (double)s->peak;
+        }
+    }
+    // fatal error or stop: fail whatever is left
+    for (auto &p : s->slots) { finish(s, p->q, s->fatal ? s->fatal : GB_EINVAL, p.get()); release_slot(s, *p); }
+    s->slots.clear();
+    for (auto &q : s->pending) finish(s, q, s->fatal ? s->fatal : GB_EINVAL, nullptr);
+    s->pending.clear();
+    cudaStreamSynchronize(s->side_st);
+    cudaStreamSynchronize(s->main_st);
+}
+
+// ================================================================= ABI ==
+extern "C" int serve_create(const ServeOptions *opt, gb_server **out) {
+    GB_REQUIRE(opt && out, "serve_create: NULL argument");
+    *out = nullptr;
+    GB_REQUIRE(opt->mem_budget >= (1u << 20), "serve_create: mem_budget below 1 MB");
+    GB_REQUIRE(opt->max_slots >= 1 && opt->max_slots <= 4096, "serve_create: max_slots not in 1..4096");
+    GB_REQUIRE(opt->precision == GB_F64 || opt->precision == GB_F32_RU,
+               "serve_create: precision must be GB_F64 or GB_F32_RU");
+    gb_server *s = new gb_server();
+    s->opt = *opt;
+    if (!(s->opt.tol > 0)) s->opt.tol = 1e-10;
+    if (s->opt.max_iter <= 0) s->opt.max_iter = 1000000;
+    if (s->opt.iters_per_step <= 0) s->opt.iters_per_step = 200;
+    if (opt->device >= 0) GB_CHECK_CUDA(cudaSetDevice(opt->device));
+    GB_CHECK_CUDA(cudaGetDevice(&s->dev));
+    GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->main_st, cudaStreamNonBlocking));
+    GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking));
+    GB_CHECK_CUDA(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+    s->alloc.ctx = s;
+    s->alloc.alloc = srv_alloc;
+    s->alloc.free = srv_free;
+    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_sys, sizeof(BSys) * s->opt.max_slots));
+    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_mask, sizeof(int) * KMAX * s->opt.max_slots));
+    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_G, sizeof(BGlobal)));
+    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_sys1, sizeof(BSys)));
+    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_mask1, sizeof(int) * KMAX));
+    s->th = std::thread(server_loop, s);
+    *out = s;
+    return GB_OK;
+}
+
+extern "C" int serve_submit(gb_server *s, const ServeRequest *r, uint64_t *ticket) {
+    GB_REQUIRE(s && r && ticket, "serve_submit: NULL argument");
+    GB_REQUIRE(r->k >= 1 && r->k <= KMAX, "serve_submit: k must be in 1..%d", KMAX);
+    GB_REQUIRE(r->h_x, "serve_submit: h_x (result buffer) is NULL");
+    GB_REQUIRE(r->h_gB || (r->gid >= 0 && r->gid <= 4), "serve_submit: need h_gB or a Dirichlet id 0..4");
+    SReq q;
+    q.r = *r;
+    const int nc = r->gid == 3 ? 4 : (r->gid == 4 ? 10 : 0);
+    if (!r->h_gB && nc) {
+        GB_REQUIRE(r->h_coef, "serve_submit: Dirichlet id %d needs coefficients", r->gid);
+        q.coef.assign(r->h_coef, r->h_coef + (size_t)nc * r->k);
+    }
+    q.t_submit = now_ms();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) { set_error("serve_submit: server is shutting down"); return GB_EINVAL; }
+    if (s->fatal) { set_error("serve_submit: server stopped after an error: %s", s->fatal_msg.c_str()); return s->fatal; }
+    q.ticket = s->next_ticket++;
+    *ticket = q.ticket;
+    s->inbox.push_back(std::move(q));
+    s->stats.submitted += 1;
+    s->cv.notify_one();
+    return GB_OK;
+}
+
+extern "C" int serve_poll(gb_server *s, uint64_t ticket, ServeResult *out) {
+    GB_REQUIRE(s && out, "serve_poll: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) {
+        if (ticket == 0 || ticket >= s->next_ticket) { set_error("serve_poll: unknown ticket %llu", (unsigned long long)ticket); return GB_EINVAL; }
+        return GB_PENDING;
+    }
+    *out = it->second;
+    s->results.erase(it);
+    return out->status;
+}
+
+extern "C" int serve_stats(gb_server *s, ServeStats *out) {
+    GB_REQUIRE(s && out, "serve_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->pending = (int64_t)(s->stats.submitted - s->stats.completed - s->stats.resident);
+    return GB_OK;
+}
+
+extern "C" void serve_destroy(gb_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+        s->cv.notify_all();
+    }
+    if (s->th.joinable()) s->th.join();
+    cudaFree(s->d_sys); cudaFree(s->d_unit_sys); cudaFree(s->d_mask); cudaFree(s->d_G); cudaFree(s->d_partials);
+    cudaFree(s->d_sys1); cudaFree(s->d_unit1); cudaFree(s->d_mask1); cudaFree(s->d_partials1);
+    cudaEventDestroy(s->ev);
+    cudaStreamDestroy(s->main_st);
+    cudaStreamDestroy(s->side_st);
+    delete s;
+}

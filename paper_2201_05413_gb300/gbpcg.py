@@ -74,6 +74,37 @@ class PcgStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ServeOptions(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_slots", C.c_int32), ("precision", C.c_int32),
+                ("tol", C.c_double), ("max_iter", C.c_int64), ("iters_per_step", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class ServeRequest(C.Structure):
+    _fields_ = [("spec", gb_fem_spec), ("k", C.c_int32), ("gid", C.c_int32),
+                ("h_coef", C.POINTER(C.c_double)), ("h_gB", C.POINTER(C.c_double)),
+                ("h_x", C.POINTER(C.c_double))]
+
+
+class ServeResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("k", C.c_int32), ("n", C.c_int64), ("iterations", C.c_int64),
+                ("updates", C.c_int32), ("reserved", C.c_int32), ("relres", C.c_double),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double), ("bytes", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("pending", C.c_int64), ("resident", C.c_int64), ("steps", C.c_int64),
+                ("mem_in_use", C.c_double), ("mem_peak", C.c_double), ("max_resident", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 _P = C.c_void_p
 _SIGS = {
     "gbpcg_last_error": (C.c_char_p, []),
@@ -95,6 +126,11 @@ _SIGS = {
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_kernel_times": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_double)]),
+    "serve_create": (C.c_int, [C.POINTER(ServeOptions), C.POINTER(_P)]),
+    "serve_submit": (C.c_int, [_P, C.POINTER(ServeRequest), C.POINTER(C.c_uint64)]),
+    "serve_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ServeResult)]),
+    "serve_stats": (C.c_int, [_P, C.POINTER(ServeStats)]),
+    "serve_destroy": (None, [_P]),
     "pcg_solve_batched": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                     C.POINTER(C.c_int), C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
 }
