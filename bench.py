@@ -6,11 +6,13 @@ Workload (one step): the two systems of the 2D jittered 1024x1024-cell mesh
 (1.05M unknowns) and P2 (4.19M unknowns), Dirichlet data g = x^2 - y^2 -- each
 assembled on the device, converted to SELL-C-sigma (C=32, sigma=256), lifted,
 and solved by fp64 Jacobi-PCG from x0 = 0 to ||b - A x|| / ||b|| <= 1e-10.
-value = solves/s (2 solves per step).  Alongside: the same step with
-fp32-inner iterative refinement, per-kernel times and the HBM roofline of the
-dominant kernel, and the CPU oracle timed on this host.
+value = solves/s (2 solves per step).  Alongside: the same step with an fp32
+recurrence and fp64 reliable updates, per-kernel times and the roofline of the
+dominant kernel, a seeded serving mix through the continuous-batching server,
+and the CPU oracle timed on this host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --profile-kernels p2 --profile-precision f64   (ncu driver)
 
 N>1 runs as torchrun ranks, one GPU each: independent replicas of the same
 workload (the path has no exchange step), max-over-ranks timing.
@@ -29,11 +31,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TOL = 1e-10
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA (4 flops) per SM per clock
 SYSTEMS = [  # (name, dim, degree, cells, jitter, diag_mode, seed)
     ("2D-P1-jittered-1024", 2, 1, 1024, 1, 1, 1),
     ("2D-P2-jittered-1024", 2, 2, 1024, 1, 1, 1),
 ]
 GID = 1  # g = x^2 - y^2
+# Iterations a full fp64 Jacobi-PCG solve of each system takes to 1e-10 (the
+# device solver runs the oracle's recurrence; the parity tests hold the two
+# counts within 2%).  The reference arm scales its per-iteration time by these.
+ITERS_FULL = [3597, 8534]
 WORKLOAD = "cfg2: 2D unit square 1024x1024 cells, jittered +-h/4, random diagonals (seed 1), P1 + P2, g=x^2-y^2"
 
 
@@ -45,6 +52,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the seeded serving mix timed after the main workload (0 = skip)")
+    ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
+                    help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
+    ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--profile-iters", type=int, default=3)
     return ap.parse_args()
 
 
@@ -177,10 +190,10 @@ def run_ours(args, rank, world):
     solves = len(SYSTEMS) * args.steps * world
     value = solves / total
 
-    # ---- mixed precision (fp32-inner refinement), same workload
+    # ---- mixed precision (fp32 recurrence, fp64 reliable updates), same workload
     mixed_info = []
-    step(precision=P.GB_F32_IR, collect=mixed_info)
-    tmx = timed(args.steps, precision=P.GB_F32_IR)
+    step(precision=P.GB_F32_RU, collect=mixed_info)
+    tmx = timed(args.steps, precision=P.GB_F32_RU)
     mixed_value = len(SYSTEMS) * args.steps / sum(tmx)
 
     # ---- e2e through the public API with host buffers
@@ -203,8 +216,11 @@ def run_ours(args, rank, world):
     # lengths, p gathered once, q written once (fp64: 8-byte values/vectors)
     spmv_bytes64 = nnz2 * (8 + 4) + n2 * (4 + 8 + 8)
     spmv_bytes32 = nnz2 * (4 + 4) + n2 * (4 + 4 + 4)
+    spmv_flops64 = 2 * (nnz2 + n2)  # one FMA per stored entry, one per row for p.q
     peak, peak_src = peaks()
     ach64 = spmv_bytes64 / (ms64[0] * 1e-3) / 1e9
+    ach32 = spmv_bytes32 / (ms32[0] * 1e-3) / 1e9
+    tf64 = spmv_flops64 / (ms64[0] * 1e-3) / 1e12
     iter_bytes64 = nnz2 * 12 + 7 * n2 * 8
     iter_ms64 = sum(ms64)
 
@@ -214,7 +230,7 @@ def run_ours(args, rank, world):
                         "relres": st["relres"], "solve_ms": round(st["solve_ms"], 3),
                         "effective_GBps": round(st["bytes_moved"] / (st["solve_ms"] * 1e-3) / 1e9, 1)})
     for (name, d, A, b, st), row in zip(mixed_info, per_sys):
-        row["f32_ir"] = {"inner_iterations": st["iterations"], "outer": st["outer"],
+        row["f32_ru"] = {"iterations": st["iterations"], "reliable_updates": st["outer"],
                          "fallback_iterations": st["fallback_iterations"], "relres": st["relres"],
                          "solve_ms": round(st["solve_ms"], 3)}
 
@@ -227,15 +243,23 @@ def run_ours(args, rank, world):
         "config": {"workload": WORKLOAD, "systems": [s[0] for s in SYSTEMS], "tol": TOL,
                    "sell": {"C": 32, "sigma": 256}, "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) before every timed step; P2 matrix 578 MB > L2"},
-        "mixed_f32_ir": {"value": round(mixed_value, 4), "unit": "solves/s", "dtype": "f32 inner / f64 outer",
+        "mixed_f32_ru": {"value": round(mixed_value, 4), "unit": "solves/s",
+                         "dtype": "f32 recurrence (fp32 values/vectors) + f64 reliable updates, test and solution",
                          "speedup_vs_f64": round(mixed_value / value * world, 3)},
         "per_system": per_sys,
         "kernel_ms": {"f64": {"spmv_pq": ms64[0], "update": ms64[1], "pupdate": ms64[2]},
                       "f32": {"spmv_pq": ms32[0], "update": ms32[1], "pupdate": ms32[2]}},
         "iteration_GBps_f64": round(iter_bytes64 / (iter_ms64 * 1e-3) / 1e9, 1),
-        "roofline": {"bound": "hbm", "kernel": "k_spmv_pq<double> (2D P2 1024^2)", "achieved": round(ach64, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(ach64 / peak, 4), "traffic": None,
-                     "peak_source": peak_src, "bytes_per_launch": spmv_bytes64},
+        "roofline": {"bound": "alu", "kernel": "k_spmv_tma<double,double> (2D P2 1024^2, fp64 SpMV + p.q)",
+                     "achieved": round(tf64, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": round(tf64 / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                     "peak_source": "fp64 FMA: 2 per SM per clock x 152 SMs x 2070 MHz (measured 1.21 TFLOP/s)",
+                     "flops_per_launch": spmv_flops64,
+                     "hbm_view": {"achieved_GBps": round(ach64, 1), "peak_GBps": peak, "frac": round(ach64 / peak, 4),
+                                  "bytes_per_launch": spmv_bytes64, "peak_source": peak_src}},
+        "roofline_mixed": {"bound": "hbm", "kernel": "k_spmv_tma<float,float> (2D P2 1024^2, fp32 SpMV + p.q)",
+                           "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s", "frac": round(ach32 / peak, 4),
+                           "traffic": None, "peak_source": peak_src, "bytes_per_launch": spmv_bytes32},
         "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
@@ -283,7 +307,7 @@ def cpu_oracle_sample(budget_s, gpu_iters=None):
 
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on this host's cores, same config/metric."""
-    gpu_iters = None
+    gpu_iters = ITERS_FULL
     vals = []
     details = None
     for _ in range(args.warmup):
@@ -292,7 +316,8 @@ def run_reference(args, rank, world):
         v, details = cpu_oracle_sample(args.cpu_sample_s, gpu_iters)
         vals.append(v)
     value = statistics.median(vals)
-    sample = "oracle assembly + bounded PCG iteration sample per system; solves/s from sec/iter x own iteration count of the sample"
+    sample = ("oracle full assembly + a bounded PCG iteration sample per system; solves/s from sec/iter "
+              f"x the iterations of a full solve ({ITERS_FULL})")
     return {
         "impl": "reference", "metric": "PCG solves/s at rel. residual 1e-10 (fp64 Jacobi-PCG), cfg2 P1+P2",
         "value": round(value, 6), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -306,8 +331,69 @@ def run_reference(args, rank, world):
     }
 
 
+PROFILE_SYSTEMS = {"p1": (2, 1, 1024, 1, 1, 1, 1), "p2": (2, 2, 1024, 1, 1, 1, 1),
+                   "3dp1": (3, 1, 128, 0, 0, 0, 2), "3dp2": (3, 2, 64, 0, 0, 0, 2)}
+
+
+def run_profile(args):
+    """Profiling driver for ncu: one system, CG kernels timed with CUDA events."""
+    import torch
+    import paper_2201_05413_gb300 as P
+    P.load()
+    dim, deg, cells, jit, dm, seed, gid = PROFILE_SYSTEMS[args.profile_kernels]
+    d = P.FemSystem(dim, deg, cells, jit, dm, seed)
+    A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32 | P.GB_VAL_BF16)
+    b = d.lift(d.dirichlet(gid))[:, 0]
+    prec = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR}[args.profile_precision]
+    ms = A.kernel_times(b, prec, args.profile_iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"system": args.profile_kernels, "precision": args.profile_precision, "n": A.n,
+                      "nnz": A.nnz, "kernel_ms": ms}))
+
+
+def run_serving(nreq, seed=4):
+    """Seeded serving mix (continuous batching, fp32 + fp64 reliable updates),
+    all requests submitted at once, against the same requests solved one at a
+    time in fp64 with pcg_solve_batched (assembly included in both)."""
+    import numpy as np
+    import torch
+    import paper_2201_05413_gb300 as P
+    from paper_2201_05413_gb300.workloads import serving_requests
+    reqs = serving_requests(nreq, seed=seed)
+    srv = P.Server(mem_budget=40 << 30, max_slots=64, precision=P.GB_F32_RU, tol=TOL)
+    t0 = time.perf_counter()
+    ts = [srv.submit(r["dim"], r["degree"], r["cells"], r["jitter"], r["diag_mode"], r["seed"],
+                     k=r["k"], gid=r["gid"], coef=r["coef"]) for r in reqs]
+    res = srv.wait(ts, timeout_s=1800)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([res[t][0]["latency_ms"] for t in ts])
+    ok = sum(1 for t in ts if res[t][0]["status"] == 0)
+    # one at a time, fp64
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in reqs:
+        d = P.FemSystem(r["dim"], r["degree"], r["cells"], r["jitter"], r["diag_mode"], r["seed"])
+        A = d.to_sell(32, 256, P.GB_VAL_F64)
+        B = d.lift(d.dirichlet(r["gid"], r["coef"], r["k"]))
+        P.pcg_solve_batched([A], [B], tol=TOL, max_iter=2000000)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    return {"requests": nreq, "seed": seed, "ok": ok, "mix": "cfg5 generator (70% 2D jittered n in [32,1024], "
+            "30% 3D Kuhn n in [16,128], P1/P2, k 1-8), all submitted at t=0",
+            "solves_per_s": round(nreq / wall, 3), "p50_ms": round(float(np.percentile(lat, 50)), 1),
+            "p99_ms": round(float(np.percentile(lat, 99)), 1), "wall_s": round(wall, 2),
+            "max_resident": stats["max_resident"], "mem_peak_GB": round(stats["mem_peak"] / 1e9, 3),
+            "one_at_a_time_f64": {"solves_per_s": round(nreq / seq, 3), "wall_s": round(seq, 2)},
+            "speedup": round(seq / wall, 3)}
+
+
 def main():
     args = parse()
+    if args.profile_kernels:
+        run_profile(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -320,6 +406,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     out, info = run_ours(args, rank, world)
+    if rank == 0 and args.serve_requests > 0:
+        out["serving"] = run_serving(args.serve_requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gpu_iters = [st["iterations"] for (_, _, _, _, st) in info]
         v, det = cpu_oracle_sample(args.cpu_sample_s, gpu_iters)
