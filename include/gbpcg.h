@@ -138,8 +138,11 @@ void fem_system_destroy(gb_fem_system *sys);
  * (padding: the row's own index, value 0).  The permutation is applied
  * symmetrically (rows and columns).  val_types: bit 0 fp64, bit 1 fp32,
  * bit 2 bf16 value copies (fp64 is always kept; fp32/bf16 serve the mixed-
- * precision inner solve).  C in {32, 64, 128}; sigma >= 1. */
-enum { GB_VAL_F64 = 1, GB_VAL_F32 = 2, GB_VAL_BF16 = 4 };
+ * precision inner solve).  GB_IDX16 (C = 32 only): also store 16-bit column
+ * deltas (column - min(row, n-1)) when they all fit; the SpMV then streams
+ * those instead of 32-bit indices (6 instead of 8 bytes per fp32 entry).
+ * C in {32, 64, 128}; sigma >= 1. */
+enum { GB_VAL_F64 = 1, GB_VAL_F32 = 2, GB_VAL_BF16 = 4, GB_IDX16 = 8 };
 
 typedef struct gb_sell gb_sell;
 
@@ -153,6 +156,8 @@ typedef struct gb_sell_info {
     const int32_t *d_col;        /* padded, new numbering */
     const double *d_val;         /* padded fp64 */
     const double *d_dinv;        /* 1/diag, new order */
+    const int16_t *d_col16;      /* GB_IDX16: column - min(row, n-1) per padded slot when every
+                                    delta fits in 16 bits (the SpMV then streams these), else NULL */
 } gb_sell_info;
 
 /* From an assembled system's K_II.  Asynchronous except for one sync to read

@@ -23,7 +23,7 @@ class _DevArray:
 
 def _view(ptr, shape, dtype):
     typestr = {torch.int32: "<i4", torch.int64: "<i8", torch.float64: "<f8",
-               torch.float32: "<f4"}[dtype]
+               torch.float32: "<f4", torch.int16: "<i2"}[dtype]
     if int(ptr or 0) == 0 or any(s == 0 for s in shape):
         return torch.empty(shape, dtype=dtype, device="cuda")
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
@@ -158,7 +158,9 @@ class Sell:
                 "row_len": _view(i.d_row_len, (self.n,), torch.int32).clone(),
                 "col": _view(i.d_col, (self.padded,), torch.int32).clone(),
                 "val": _view(i.d_val, (self.padded,), torch.float64).clone(),
-                "dinv": _view(i.d_dinv, (self.n,), torch.float64).clone()}
+                "dinv": _view(i.d_dinv, (self.n,), torch.float64).clone(),
+                "col16": (None if not i.d_col16 else
+                          _view(i.d_col16, (self.padded,), torch.int16).clone())}
 
     def spmv(self, x):
         y = torch.empty_like(x)

@@ -26,7 +26,7 @@ namespace gb {
 
 // q = A p with TMA-staged slices (spmv_tma.cuh), one warp per balanced chunk
 // range, then the same p.q reduction and alpha as k_spmv_pq.
-template <class TV, class TX>
+template <class TV, class TX, class TI>
 __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restrict__ val,
                                                  const TX *__restrict__ p, TX *__restrict__ q,
                                                  double *partials, PcgScal *S) {
@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restric
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double sm[NT / 32];
     constexpr int NB = TmaDepth<TV>::NB;
-    TmaRing<TV, NB> *bufs = reinterpret_cast<TmaRing<TV, NB> *>(smem_raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + TMA_WARPS * sizeof(TmaRing<TV, NB>));
+    TmaRing<TV, NB, TI> *bufs = reinterpret_cast<TmaRing<TV, NB, TI> *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + TMA_WARPS * sizeof(TmaRing<TV, NB, TI>));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         for (int b = 0; b < NB; ++b) mbar_init(&bars[NB * warp + b], 1);
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restric
     const int gw = blockIdx.x * TMA_WARPS + warp;
     const int c0 = __ldg(A.warp_chunk + gw), c1 = __ldg(A.warp_chunk + gw + 1);
     bool timed_out = false;
-    const TX dot = spmv_warp_stream<TV, TX, NB>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
+    const TX dot = spmv_warp_stream<TV, TX, NB, TI>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
     if (timed_out && lane == 0) atomicExch(&S->err, 1);
     const double t = block_sum<NT>((double)dot, sm);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
@@ -65,16 +65,27 @@ __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restric
     }
 }
 
+template <class TV, class TX, class TI>
+static void launch_spmv_tma_t(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+                              PcgScal *S, cudaStream_t st) {
+    static bool attr_set = false;  // per instantiation
+    const int smem = (int)tma_smem_bytes<TV, TI>();
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_spmv_tma<TV, TX, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    ::gb::count_launches(1); k_spmv_tma<TV, TX, TI><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+}
+
+// 16-bit column deltas when the matrix has them, 32-bit indices otherwise
 template <class TV, class TX>
 static void launch_spmv_tma(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
                             PcgScal *S, cudaStream_t st) {
-    static bool attr_set = false;  // per instantiation
-    const int smem = (int)tma_smem_bytes<TV>();
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_spmv_tma<TV, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
-    }
-    ::gb::count_launches(1); k_spmv_tma<TV, TX><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+#ifndef GB_TMA_NO_COL16
+    if (A.col16) launch_spmv_tma_t<TV, TX, int16_t>(A, val, p, q, partials, S, st);
+    else
+#endif
+        launch_spmv_tma_t<TV, TX, int32_t>(A, val, p, q, partials, S, st);
 }
 
 // ------------------------------------------------------------ kernels --
@@ -137,11 +148,17 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
     }
 }
 
-// Two elements per thread per step (16-byte loads for fp64, 8-byte for fp32);
-// n odd: the last element is handled by the thread that owns the last pair.
 template <class TX> struct Vec2;
 template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
+
+// Grid-stride over element pairs, UPD_U pairs per thread per step with every
+// load issued before the arithmetic (memory-level parallelism for these
+// streaming kernels); the odd last element, if any, goes to thread 0.
+#ifndef GB_UPD_U
+#define GB_UPD_U 2
+#endif
+constexpr int UPD_U = GB_UPD_U;
 
 template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX *__restrict__ r,
@@ -155,22 +172,37 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
     const TX alpha = (TX)S->alpha;
     TX rz = TX(0), rr = TX(0);
     const int64_t npair = n >> 1;
-    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < npair; i += (int64_t)gridDim.x * NT) {
-        V2 xv = reinterpret_cast<V2 *>(x)[i];
-        V2 rv = reinterpret_cast<V2 *>(r)[i];
-        const V2 pv = reinterpret_cast<const V2 *>(p)[i];
-        const V2 qv = reinterpret_cast<const V2 *>(q)[i];
-        const D2 dv = reinterpret_cast<const D2 *>(dinv)[i];
-        xv.x += alpha * pv.x;
-        xv.y += alpha * pv.y;
-        rv.x -= alpha * qv.x;
-        rv.y -= alpha * qv.y;
-        reinterpret_cast<V2 *>(x)[i] = xv;
-        reinterpret_cast<V2 *>(r)[i] = rv;
-        rz += rv.x * ((TX)dv.x * rv.x);
-        rz += rv.y * ((TX)dv.y * rv.y);
-        rr += rv.x * rv.x;
-        rr += rv.y * rv.y;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < npair; i0 += stride * UPD_U) {
+        V2 xv[UPD_U], rv[UPD_U], pv[UPD_U], qv[UPD_U];
+        D2 dv[UPD_U];
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < npair) {
+                xv[u] = reinterpret_cast<V2 *>(x)[i];
+                rv[u] = reinterpret_cast<V2 *>(r)[i];
+                pv[u] = reinterpret_cast<const V2 *>(p)[i];
+                qv[u] = reinterpret_cast<const V2 *>(q)[i];
+                dv[u] = reinterpret_cast<const D2 *>(dinv)[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < npair) {
+                xv[u].x += alpha * pv[u].x;
+                xv[u].y += alpha * pv[u].y;
+                rv[u].x -= alpha * qv[u].x;
+                rv[u].y -= alpha * qv[u].y;
+                reinterpret_cast<V2 *>(x)[i] = xv[u];
+                reinterpret_cast<V2 *>(r)[i] = rv[u];
+                rz += rv[u].x * ((TX)dv[u].x * rv[u].x);
+                rz += rv[u].y * ((TX)dv[u].y * rv[u].y);
+                rr += rv[u].x * rv[u].x;
+                rr += rv[u].y * rv[u].y;
+            }
+        }
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
         const int64_t i = n - 1;
@@ -213,13 +245,28 @@ __global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, c
     using D2 = typename Vec2<TD>::T;
     const TX beta = (TX)S->beta;
     const int64_t npair = n >> 1;
-    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < npair; i += (int64_t)gridDim.x * NT) {
-        V2 pv = reinterpret_cast<V2 *>(p)[i];
-        const V2 rv = reinterpret_cast<const V2 *>(r)[i];
-        const D2 dv = reinterpret_cast<const D2 *>(dinv)[i];
-        pv.x = (TX)dv.x * rv.x + beta * pv.x;
-        pv.y = (TX)dv.y * rv.y + beta * pv.y;
-        reinterpret_cast<V2 *>(p)[i] = pv;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < npair; i0 += stride * UPD_U) {
+        V2 pv[UPD_U], rv[UPD_U];
+        D2 dv[UPD_U];
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < npair) {
+                pv[u] = reinterpret_cast<V2 *>(p)[i];
+                rv[u] = reinterpret_cast<const V2 *>(r)[i];
+                dv[u] = reinterpret_cast<const D2 *>(dinv)[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < npair) {
+                pv[u].x = (TX)dv[u].x * rv[u].x + beta * pv[u].x;
+                pv[u].y = (TX)dv[u].y * rv[u].y + beta * pv[u].y;
+                reinterpret_cast<V2 *>(p)[i] = pv[u];
+            }
+        }
     }
     if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = (TX)dinv[n - 1] * r[n - 1] + beta * p[n - 1];
 }
@@ -384,7 +431,7 @@ static Grids pick_grids(int64_t n, int C) {
     Grids g;
     const int64_t warps = ((n + C - 1) / C) * (C / 32);
     g.spmv = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (warps + 7) / 8));
-    g.vec = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (n + NT - 1) / NT));
+    g.vec = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (n + 2 * NT * UPD_U - 1) / (2 * NT * UPD_U)));
     return g;
 }
 
@@ -709,6 +756,7 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
     double bytes = 0.0;
     const double sval = sizeof(TV);
     bool first = true;
+    long long last_cycle = 0;
     {
         PcgScal hs{};
         hs.maxit = o.max_iter;
@@ -730,10 +778,13 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         GB_TRY(read_scal(w.S2, &hr, st));
         if (hr.done) break;  // r32 == 0 or not positive: nothing to iterate on
         {
-            // run until ||r32||^2 <= max(delta^2 ||r32_0||^2, target)
+            // run until ||r32||^2 <= max(delta^2 ||r32_0||^2, target), or for at
+            // most a cycle budget (a recurrence that stagnates above the
+            // threshold still reaches the fp64 update and the stall test)
             const double th = std::max(RU_DELTA * RU_DELTA * hr.rr, target2);
             GB_CHECK_CUDA(cudaMemcpyAsync(&w.S2->thresh, &th, sizeof(double), cudaMemcpyHostToDevice, st));
-            const long long mx = o.max_iter;
+            const long long cap = 1000 + 3 * last_cycle;
+            const long long mx = std::min<long long>(o.max_iter, hr.it + cap);
             GB_CHECK_CUDA(cudaMemcpyAsync(&w.S2->maxit, &mx, sizeof(long long), cudaMemcpyHostToDevice, st));
         }
         const long long it0 = hr.it;
@@ -745,6 +796,7 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         PcgScal hi{};
         GB_TRY(read_scal(w.S2, &hi, st));
         const long long dit = hi.it - it0;
+        if (hi.status == ST_CONV) last_cycle = dit;  // the last cycle that reached its threshold
         inner_total = hi.it;
         launches += 3 * dit;
         bytes += dit * ((double)A->nnz * (sval + 4.0) + 7.0 * n * 4.0);
@@ -756,8 +808,13 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         GB_TRY(read_scal(w.S, &h, st));
         rel = std::sqrt(h.rr / h.bb);
         ++updates;
-        if (hi.status == ST_BREAK || hi.status == ST_MAXIT) break;
-        if (!(rel < 0.9 * prev)) { if (++stalls >= 3) break; } else stalls = 0;
+        if (getenv("GBPCG_LOG"))
+            fprintf(stderr, "[gbpcg ru] update %d: cycle its %lld status %d rel %.3e best %.3e\n", updates, dit,
+                    hi.status, rel, prev);
+        if (hi.status == ST_BREAK || inner_total >= o.max_iter) break;
+        // a cycle that ran out of its budget, or an update without a 10% gain,
+        // is a stall; two in a row hand the solve to the fp64 finish
+        if (hi.status == ST_MAXIT || !(rel < 0.9 * prev)) { if (++stalls >= 2) break; } else stalls = 0;
         prev = std::min(prev, rel);
     }
     stats->iterations = inner_total;

@@ -119,6 +119,30 @@ __global__ void k_sell_fill(int64_t n, int64_t nchunks, int C, const int32_t *pe
     }
 }
 
+// 16-bit column deltas for the TMA SpMV: delta = col - min(row, n-1) for every
+// padded slot (padding: the row itself, delta 0; rows past n point at n-1).
+// *overflow is set if a delta does not fit in int16 (the matrix then keeps
+// int32 indices only).
+__global__ void k_col_delta(int64_t n, int64_t nchunks, const int64_t *chunk_ptr, const int32_t *chunk_w,
+                            const int32_t *col, int16_t *col16, int *overflow) {
+    const int64_t rows = nchunks * 32;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = r >> 5;
+        const int t = (int)(r & 31);
+        const int w = chunk_w[c];
+        const int64_t base = chunk_ptr[c] + t;
+        const int64_t rb = r < n ? r : n - 1;
+        bool bad = false;
+        for (int j = 0; j < w; ++j) {
+            const int64_t k = base + (int64_t)j * 32;
+            int64_t d = r < n ? (int64_t)col[k] - rb : 0;
+            if (d < -32768 || d > 32767) { bad = true; d = 0; }
+            col16[k] = (int16_t)d;
+        }
+        if (bad) atomicExch(overflow, 1);
+    }
+}
+
 // Warp w of the TMA SpMV owns chunks [warp_chunk[w], warp_chunk[w+1]): the
 // first chunk whose start is at or after w/nw of the padded nonzeros.
 __global__ void k_warp_partition(int64_t nchunks, const int64_t *chunk_ptr, int64_t padded, int nw,
@@ -143,7 +167,7 @@ static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const dou
     GB_REQUIRE(n >= 1, "csr_to_sell: empty matrix");
     GB_REQUIRE(C == 32 || C == 64 || C == 128, "csr_to_sell: C must be 32, 64 or 128");
     GB_REQUIRE(sigma >= 1, "csr_to_sell: sigma must be >= 1");
-    GB_REQUIRE((val_types & ~7) == 0, "csr_to_sell: unknown val_types bits");
+    GB_REQUIRE((val_types & ~15) == 0, "csr_to_sell: unknown val_types bits");
     gb_sell *A = new gb_sell();
     A->mem = Mem(alloc, st);
     Mem &mem = A->mem;
@@ -214,6 +238,16 @@ static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const dou
         n, A->nchunks, C, A->perm, A->iperm, rp, ci, v, A->chunk_ptr, A->chunk_w, A->col, A->val,
         A->val32, A->val16);
     STEPC(cudaGetLastError());
+    if (C == 32 && (val_types & GB_IDX16)) {  // 16-bit column deltas where they fit
+        STEP(mem.alloc_n(&A->col16, padded));
+        STEPC(cudaMemsetAsync(flags, 0, sizeof(int), st));
+        ::gb::count_launches(1); k_col_delta<<<stride_grid(A->nchunks * 32, 256, 8), 256, 0, st>>>(
+            n, A->nchunks, A->chunk_ptr, A->chunk_w, A->col, A->col16, flags);
+        STEPC(cudaGetLastError());
+        STEPC(cudaMemcpyAsync(hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        STEPC(cudaStreamSynchronize(st));
+        if (hflags[0]) { mem.release(A->col16); A->col16 = nullptr; }
+    }
     if (C == 32) {  // chunk ranges of the TMA-staged SpMV (one per warp of its fixed grid)
         A->nwarps = num_sms() * TMA_BLOCKS_PER_SM * 8;
         STEP(mem.alloc_n(&A->warp_chunk, (size_t)A->nwarps + 1));
@@ -302,6 +336,7 @@ extern "C" int sell_info(const gb_sell *A, gb_sell_info *o) {
     o->C = A->C; o->sigma = A->sigma; o->max_row = A->max_row; o->reserved = 0;
     o->d_perm = A->perm; o->d_chunk_ptr = A->chunk_ptr; o->d_chunk_w = A->chunk_w;
     o->d_row_len = A->row_len; o->d_col = A->col; o->d_val = A->val; o->d_dinv = A->dinv;
+    o->d_col16 = A->col16;
     return GB_OK;
 }
 
@@ -330,6 +365,6 @@ extern "C" void sell_destroy(gb_sell *A) {
     m.release(A->perm); m.release(A->iperm); m.release(A->row_len);
     m.release(A->dinv); m.release(A->dinv32);
     m.release(A->chunk_w); m.release(A->chunk_ptr); m.release(A->warp_chunk);
-    m.release(A->col); m.release(A->val); m.release(A->val32); m.release(A->val16);
+    m.release(A->col); m.release(A->col16); m.release(A->val); m.release(A->val32); m.release(A->val16);
     delete A;
 }

@@ -21,6 +21,7 @@ struct SellView {
     const int32_t *chunk_w;
     const int32_t *warp_chunk;  // nwarps+1 chunk bounds, balanced by padded nonzeros (C == 32)
     int nwarps;
+    const int16_t *col16;       // column - min(row, n-1) per padded slot, or null (C == 32)
 };
 
 }  // namespace gb
@@ -30,6 +31,7 @@ struct gb_sell {
     int C = 32, sigma = 1, max_row = 0;
     int32_t *perm = nullptr, *iperm = nullptr, *row_len = nullptr, *chunk_w = nullptr, *col = nullptr;
     int32_t *warp_chunk = nullptr;
+    int16_t *col16 = nullptr;
     int nwarps = 0;
     int64_t *chunk_ptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
@@ -38,6 +40,6 @@ struct gb_sell {
     gb::Mem mem;
     gb::SellView view() const {
         return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32,
-                            chunk_w, warp_chunk, nwarps};
+                            chunk_w, warp_chunk, nwarps, col16};
     }
 };

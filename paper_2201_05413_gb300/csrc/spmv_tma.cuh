@@ -28,6 +28,9 @@ namespace gb {
 #ifndef GB_TMA_NB32
 #define GB_TMA_NB32 3
 #endif
+#ifndef GB_TMA_PREFETCH
+#define GB_TMA_PREFETCH 0  // stages beyond the ring prefetched into L2 (0 = off)
+#endif
 constexpr int SJ = GB_TMA_SJ;  // column-steps per staged slice
 constexpr int TMA_WARPS = 8;   // warps per block (TMA_BLOCKS_PER_SM blocks per SM)
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;  // 2 s
@@ -83,6 +86,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -90,15 +96,16 @@ __device__ __forceinline__ void fence_proxy_async() {
 // ring depth (stages in flight per warp): fp64 stages are 3 KB, fp32 2 KB, bf16 1.5 KB
 template <class TV> struct TmaDepth { static constexpr int NB = sizeof(TV) == 8 ? GB_TMA_NB64 : GB_TMA_NB32; };
 
-template <class TV, int NB>
+// TI: int32_t (column indices) or int16_t (column - min(row, n-1) deltas)
+template <class TV, int NB, class TI = int32_t>
 struct TmaRing {
-    int32_t col[NB][SJ * 32];
+    TI col[NB][SJ * 32];
     TV val[NB][SJ * 32];
 };
 
-template <class TV>
+template <class TV, class TI = int32_t>
 constexpr size_t tma_smem_bytes() {
-    return TMA_WARPS * sizeof(TmaRing<TV, TmaDepth<TV>::NB>) + TMA_WARPS * TmaDepth<TV>::NB * sizeof(uint64_t);
+    return TMA_WARPS * sizeof(TmaRing<TV, TmaDepth<TV>::NB, TI>) + TMA_WARPS * TmaDepth<TV>::NB * sizeof(uint64_t);
 }
 
 template <class TX> __device__ __forceinline__ TX ldg_vec(const TX *p) { return __ldg(p); }
@@ -116,11 +123,13 @@ __device__ __forceinline__ TX to_tx(TV v) {
 // Inside a stage the SJ gathers of p are issued first, then the products are
 // accumulated; a chunk ends when its column counter reaches the chunk width.
 // Returns the warp's partial p.q (per lane); *timed_out on a wait that ran out.
-template <class TV, class TX, int NB>
+template <class TV, class TX, int NB, class TI>
 __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__restrict__ val,
                                                const TX *__restrict__ p, TX *__restrict__ q,
-                                               int c0, int c1, TmaRing<TV, NB> &sm, uint64_t *bars,
+                                               int c0, int c1, TmaRing<TV, NB, TI> &sm, uint64_t *bars,
                                                bool *timed_out) {
+    constexpr bool DELTA = sizeof(TI) == 2;
+    const TI *colsrc = DELTA ? (const TI *)A.col16 : (const TI *)A.col;
     const int lane = threadIdx.x & 31;
     TX dot = TX(0);
     if (c0 >= c1) return dot;
@@ -132,11 +141,19 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
             const int b = (int)(st % NB);
             const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
             const int64_t off = e0 + st * SJ * 32;
-            const uint32_t bc = (uint32_t)(sj * 32 * sizeof(int32_t));
+            const uint32_t bc = (uint32_t)(sj * 32 * sizeof(TI));
             const uint32_t bv = (uint32_t)(sj * 32 * sizeof(TV));
             mbar_expect_tx(&bars[b], bc + bv);
-            bulk_g2s(sm.col[b], A.col + off, bc, &bars[b]);
+            bulk_g2s(sm.col[b], colsrc + off, bc, &bars[b]);
             bulk_g2s(sm.val[b], val + off, bv, &bars[b]);
+            if (GB_TMA_PREFETCH > 0 && st + GB_TMA_PREFETCH < nstages) {
+                // warm L2 with a stage beyond the ring: more bytes in flight than shared memory holds
+                const int64_t pst = st + GB_TMA_PREFETCH;
+                const int psj = (int)min((int64_t)SJ, nsteps - pst * SJ);
+                const int64_t poff = e0 + pst * SJ * 32;
+                bulk_prefetch_l2(colsrc + poff, (uint32_t)(psj * 32 * sizeof(TI)));
+                bulk_prefetch_l2(val + poff, (uint32_t)(psj * 32 * sizeof(TV)));
+            }
         }
     };
     for (int64_t st = 0; st < nstages && st < NB; ++st) issue(st);
@@ -150,6 +167,7 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
     }
     int64_t r = (int64_t)c * 32 + lane;
     int L = r < A.n ? __ldg(A.row_len + r) : 0;
+    int32_t rb = (int32_t)(r < A.n ? r : A.n - 1);  // base of the column deltas
     int j = 0;
     TX acc = TX(0);
     int64_t st_fail = -1;
@@ -166,9 +184,27 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
         }
         const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
         TX pv[SJ];
+        {
+            // gather pass: a stage may cross chunk boundaries, so 16-bit
+            // deltas take the row base of the chunk each step belongs to
+            int jg = j, wg = w, cg = c;
+            int32_t rbg = rb;
 #pragma unroll
-        for (int jj = 0; jj < SJ; ++jj)
-            if (jj < sj) pv[jj] = __ldg(p + sm.col[b][jj * 32 + lane]);
+            for (int jj = 0; jj < SJ; ++jj)
+                if (jj < sj) {
+                    const int32_t cj = DELTA ? rbg + (int32_t)sm.col[b][jj * 32 + lane] : (int32_t)sm.col[b][jj * 32 + lane];
+                    pv[jj] = __ldg(p + cj);
+                    if (DELTA && ++jg == wg) {
+                        jg = 0;
+                        do {
+                            ++cg;
+                            wg = cg < c1 ? __ldg(A.chunk_w + cg) : 1;
+                        } while (wg == 0);
+                        const int64_t rr = (int64_t)cg * 32 + lane;
+                        rbg = (int32_t)(rr < A.n ? rr : A.n - 1);
+                    }
+                }
+        }
 #pragma unroll
         for (int jj = 0; jj < SJ; ++jj) {
             if (jj < sj) {
@@ -190,6 +226,7 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
                     }
                     r = (int64_t)c * 32 + lane;
                     L = (c < c1 && r < A.n) ? __ldg(A.row_len + r) : 0;
+                    rb = (int32_t)(r < A.n ? r : A.n - 1);
                 }
             }
         }

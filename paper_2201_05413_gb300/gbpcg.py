@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libgbpcg.so")
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA = 0, -1, -2, -3
 GB_NOT_CONVERGED, GB_BREAKDOWN, GB_TIMEOUT, GB_TOO_LARGE, GB_PENDING = -4, -5, -6, -7, 1
-GB_VAL_F64, GB_VAL_F32, GB_VAL_BF16 = 1, 2, 4
+GB_VAL_F64, GB_VAL_F32, GB_VAL_BF16, GB_IDX16 = 1, 2, 4, 8
 GB_F64, GB_F32_IR, GB_BF16_IR, GB_F32_RU, GB_BF16_RU = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "NOT_CONVERGED",
                 -5: "BREAKDOWN", -6: "TIMEOUT", -7: "TOO_LARGE", 1: "PENDING"}
@@ -55,7 +55,7 @@ class gb_sell_info(C.Structure):
                 ("C", C.c_int32), ("sigma", C.c_int32), ("max_row", C.c_int32), ("reserved", C.c_int32),
                 ("d_perm", C.c_void_p), ("d_chunk_ptr", C.c_void_p), ("d_chunk_w", C.c_void_p),
                 ("d_row_len", C.c_void_p), ("d_col", C.c_void_p), ("d_val", C.c_void_p),
-                ("d_dinv", C.c_void_p)]
+                ("d_dinv", C.c_void_p), ("d_col16", C.c_void_p)]
 
 
 class PcgOptions(C.Structure):
