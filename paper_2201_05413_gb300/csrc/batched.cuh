@@ -85,11 +85,23 @@ __device__ __forceinline__ double col_block_sum(double v, double *smem, int kw) 
     return s;
 }
 
-// deterministic per-column sum of a system's unit partials
-__device__ __forceinline__ double col_unit_sum(const double *partials, int unit0, int nunits, int j, int slot) {
+// Per-column sum of a system's unit partials by the whole block: thread t
+// sums units t/kw, t/kw + NT/kw, ... of column t%kw, then column j adds the
+// NT/kw part sums in order.  Fixed order: deterministic.  All threads call;
+// the result is valid in threads j < kw.  stride = partial slots per unit.
+__device__ __forceinline__ double col_unit_sum_block(const double *partials, int unit0, int nunits, int slot,
+                                                     int stride, int kw, double *smem) {
+    const int j = threadIdx.x % kw, part = threadIdx.x / kw, nparts = NT / kw;
     double s = 0.0;
-    for (int u = 0; u < nunits; ++u) s += __ldcg(partials + ((size_t)(unit0 + u) * 2 + slot) * KMAX + j);
-    return s;
+    for (int u = part; u < nunits; u += nparts) s += __ldcg(partials + ((size_t)(unit0 + u) * stride + slot) * KMAX + j);
+    __syncthreads();
+    smem[threadIdx.x] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < (unsigned)kw)
+        for (int q = 0; q < nparts; ++q) t += smem[q * kw + threadIdx.x];
+    __syncthreads();
+    return t;
 }
 
 template <class T> __device__ __forceinline__ float ldv(const T *p);
@@ -103,58 +115,152 @@ __device__ __forceinline__ TX ldval_as(const TV *p) {
 }
 
 // ---------------------------------------------------------------- SpMM --
+// Q = A P for the active columns.  A group of lanes owns one row; lane l of
+// the group owns VW consecutive columns (VW = 4 fp32 / 2 fp64 when k allows
+// 16-byte row segments, else 1), so one gather P[col][VW l .. VW l + VW) is one
+// vector load feeding VW FMAs.  The group's lanes load as many of the row's
+// entries at once, broadcast them within the group with shuffles and issue
+// the gathers back to back, so the index load is off the gathers' critical
+// path.  Warps process 32/group rows side by side.
+template <class TX, int VW> struct VecN;
+template <> struct VecN<double, 1> { using T = double; };
+template <> struct VecN<double, 2> { using T = double2; };
+template <> struct VecN<float, 1> { using T = float; };
+template <> struct VecN<float, 2> { using T = float2; };
+template <> struct VecN<float, 4> { using T = float4; };
+
+template <class V> __device__ __forceinline__ void vfma(V &acc, float v, const V &p);
+template <> __device__ __forceinline__ void vfma<float>(float &a, float v, const float &p) { a += v * p; }
+template <> __device__ __forceinline__ void vfma<float2>(float2 &a, float v, const float2 &p) { a.x += v * p.x; a.y += v * p.y; }
+template <> __device__ __forceinline__ void vfma<float4>(float4 &a, float v, const float4 &p) {
+    a.x += v * p.x; a.y += v * p.y; a.z += v * p.z; a.w += v * p.w;
+}
+__device__ __forceinline__ void vfmad(double &a, double v, const double &p) { a += v * p; }
+__device__ __forceinline__ void vfmad(double2 &a, double v, const double2 &p) { a.x += v * p.x; a.y += v * p.y; }
+template <class V, class TX> __device__ __forceinline__ void vfma_any(V &a, TX v, const V &p) {
+    if constexpr (sizeof(TX) == 8) vfmad(a, v, p); else vfma<V>(a, v, p);
+}
+template <class V> __device__ __forceinline__ V vzero() { V v; memset(&v, 0, sizeof(V)); return v; }
+template <class V, class TX> __device__ __forceinline__ TX vdot(const V &a, const V &b) {
+    const TX *x = reinterpret_cast<const TX *>(&a), *y = reinterpret_cast<const TX *>(&b);
+    TX t = TX(0);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(V) / sizeof(TX)); ++i) t += x[i] * y[i];
+    return t;
+}
+
+// columns per lane for a system: the widest of 4 (fp32) / 2 (fp64) that divides k
+template <class TX> __host__ __device__ __forceinline__ int vec_width(int k) {
+    if (sizeof(TX) == 4) return (k % 4 == 0) ? 4 : ((k % 2 == 0) ? 2 : 1);
+    return (k % 2 == 0) ? 2 : 1;
+}
+
+template <class TX, class TV, int VW>
+__device__ __forceinline__ void bspmm_rows(BSys &S, int k, double *colsum /* per-lane dot partials, VW */) {
+    using V = typename VecN<TX, VW>::T;
+    const int kv = k / VW;                 // vector columns
+    int gw = 1;
+    while (gw < kv) gw <<= 1;              // lanes per row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
+    bool on = jv < kv;
+    if (on) {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < VW; ++u) any |= !S.c.done[jv * VW + u];
+        on = any;
+    }
+    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
+    const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
+    const V *P = reinterpret_cast<const V *>(S.P);
+    V *Q = reinterpret_cast<V *>(S.Q);
+    const TV *val = (const TV *)S.val;
+    const int C = S.A.C;
+    for (int64_t rb = r0 + (int64_t)warp * gpw; rb < r1; rb += (int64_t)(NT / 32) * gpw) {
+        const int64_t r = rb + grp;
+        const bool rv = r < r1;
+        const int L = rv ? S.A.row_len[r] : 0;
+        const int64_t c = rv ? r / C : 0;
+        const int64_t base = rv ? S.A.chunk_ptr[c] + (r - c * C) : 0;
+        const int Lmax = __reduce_max_sync(0xffffffffu, L);
+        V acc = vzero<V>();
+        constexpr int PRE = 4;  // entries each lane holds: one round trip for rows up to PRE*gw long
+        for (int e0 = 0; e0 < Lmax; e0 += PRE * gw) {
+            int mycol[PRE];
+            TX myval[PRE];
+#pragma unroll
+            for (int q = 0; q < PRE; ++q) {
+                const int e = e0 + q * gw + jv;
+                mycol[q] = 0;
+                myval[q] = TX(0);
+                if (e < L) {
+                    mycol[q] = __ldg(S.A.col + base + (int64_t)e * C);
+                    myval[q] = ldval_as<TX>(val + base + (int64_t)e * C);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < PRE; ++q) {
+                const int eq = e0 + q * gw;
+                if (eq >= Lmax) break;
+                const int nb = min(gw, Lmax - eq);
+#pragma unroll 8
+                for (int ee = 0; ee < nb; ++ee) {
+                    const int src = grp * gw + ee;
+                    const int cc = __shfl_sync(0xffffffffu, mycol[q], src);
+                    const TX vv = __shfl_sync(0xffffffffu, myval[q], src);
+                    if (on && eq + ee < L) vfma_any<V, TX>(acc, vv, P[(int64_t)cc * kv + jv]);
+                }
+            }
+        }
+        if (rv && on) {
+            Q[r * kv + jv] = acc;
+            const V pr = P[r * kv + jv];
+            const TX *a = reinterpret_cast<const TX *>(&acc), *b = reinterpret_cast<const TX *>(&pr);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) colsum[u] += (double)(a[u] * b[u]);
+        }
+    }
+}
+
 template <class TX, class TV>
-__global__ void __launch_bounds__(NT) k_bspmm(BSys *sys, const int *unit_sys, BGlobal *G, double *partials) {
+__global__ void __launch_bounds__(NT, 4) k_bspmm(BSys *sys, const int *unit_sys, BGlobal *G, double *partials) {
     if (G->done) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && G->use_cond) cudaGraphSetConditional(G->cond, 0);
         return;
     }
     __shared__ double sm[NT];
+    __shared__ double csum[NT / 32 * KMAX];  // per warp, per column
     const int s = unit_sys[blockIdx.x];
     BSys &S = sys[s];
     if (S.active == 0) return;
     const int k = S.k, kw = S.kw;
-    const int j = threadIdx.x % kw, grp = threadIdx.x / kw, ngrp = NT / kw;
-    const bool on = j < k && !S.c.done[j];
-    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
-    const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
-    const TX *P = (const TX *)S.P;
-    TX *Q = (TX *)S.Q;
-    const TV *val = (const TV *)S.val;
-    const int C = S.A.C;
-    TX dot = TX(0);
-    if (on) {
-        for (int64_t r = r0 + grp; r < r1; r += ngrp) {
-            const int64_t c = r / C;
-            const int L = S.A.row_len[r];
-            const int64_t base = S.A.chunk_ptr[c] + (r - c * C);
-            TX acc = TX(0);
-            int jj = 0;
-            for (; jj + 4 <= L; jj += 4) {
-                const int64_t b0 = base + (int64_t)jj * C;
-                const int c0 = __ldg(S.A.col + b0), c1 = __ldg(S.A.col + b0 + C);
-                const int c2 = __ldg(S.A.col + b0 + 2 * C), c3 = __ldg(S.A.col + b0 + 3 * C);
-                const TX v0 = ldval_as<TX>(val + b0), v1 = ldval_as<TX>(val + b0 + C);
-                const TX v2 = ldval_as<TX>(val + b0 + 2 * C), v3 = ldval_as<TX>(val + b0 + 3 * C);
-                acc += v0 * P[(int64_t)c0 * k + j];
-                acc += v1 * P[(int64_t)c1 * k + j];
-                acc += v2 * P[(int64_t)c2 * k + j];
-                acc += v3 * P[(int64_t)c3 * k + j];
-            }
-            for (; jj < L; ++jj) {
-                const int64_t b0 = base + (int64_t)jj * C;
-                acc += ldval_as<TX>(val + b0) * P[(int64_t)__ldg(S.A.col + b0) * k + j];
-            }
-            Q[r * k + j] = acc;
-            dot += P[r * k + j] * acc;
-        }
+    const int VW = vec_width<TX>(k);
+    double colsum[4] = {0.0, 0.0, 0.0, 0.0};
+    if (VW == 4) bspmm_rows<TX, TV, (sizeof(TX) == 4 ? 4 : 2)>(S, k, colsum);
+    else if (VW == 2) bspmm_rows<TX, TV, 2>(S, k, colsum);
+    else bspmm_rows<TX, TV, 1>(S, k, colsum);
+    // per-column p.q over the block in a fixed order: lanes -> warp slots -> warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kv = k / VW;
+    int gw = 1;
+    while (gw < kv) gw <<= 1;
+    const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
+    for (int i = threadIdx.x; i < NT / 32 * KMAX; i += NT) csum[i] = 0.0;
+    __syncthreads();
+    for (int g = 0; g < gpw; ++g) {  // groups of a warp add in order
+        if (grp == g && jv < kv)
+            for (int u = 0; u < VW; ++u) csum[warp * KMAX + jv * VW + u] += colsum[u];
+        __syncwarp();
     }
-    const double t = col_block_sum((double)dot, sm, kw);
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < (unsigned)k)
+        for (int w = 0; w < NT / 32; ++w) t += csum[w * KMAX + threadIdx.x];
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = t;
     if (sys_arrive_last(&S.ticket, S.nunits)) {
+        const double pq = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
         if (threadIdx.x < (unsigned)k && !S.c.done[threadIdx.x]) {
             const int jj = threadIdx.x;
-            const double pq = col_unit_sum(partials, S.unit0, S.nunits, jj, 0);
             S.c.pq[jj] = pq;
             if (!(pq > 0.0) || !isfinite(pq)) { S.c.status[jj] = ST_BREAK; S.c.done[jj] = 1; }
             else S.c.alpha[jj] = S.c.rho[jj] / pq;
@@ -168,44 +274,122 @@ __global__ void __launch_bounds__(NT) k_bspmm(BSys *sys, const int *unit_sys, BG
 }
 
 // --------------------------------------------------------------- update --
+// X += alpha P, R -= alpha Q per active column, with the fp64 partial sums of
+// R.D^-1 R and R.R; lanes own VW consecutive columns of a row (vector loads),
+// groups of lanes own rows.  The system's last block reduces in a fixed order.
+template <class TX, int VW>
+__device__ __forceinline__ void bupdate_rows(BSys &S, int k, double *rz_out, double *rr_out) {
+    TX rz[VW], rr[VW];  // per-lane partial sums in the recurrence's precision
+#pragma unroll
+    for (int u = 0; u < VW; ++u) { rz[u] = TX(0); rr[u] = TX(0); }
+    using V = typename VecN<TX, VW>::T;
+    const int kv = k / VW;
+    int gw = 1;
+    while (gw < kv) gw <<= 1;
+    const int jv = (threadIdx.x & 31) % gw, grp = threadIdx.x / gw, ngrp = NT / gw;
+    if (jv >= kv) return;
+    TX alpha[VW];
+    bool on[VW];
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+        on[u] = !S.c.done[jv * VW + u];
+        alpha[u] = on[u] ? (TX)S.c.alpha[jv * VW + u] : TX(0);
+        any |= on[u];
+    }
+    if (!any) return;
+    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
+    const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
+    struct Flush {  // hand the partial sums out on every return path
+        TX *a, *b;
+        double *oa, *ob;
+        __device__ ~Flush() {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) { oa[u] = (double)a[u]; ob[u] = (double)b[u]; }
+        }
+    } flush{rz, rr, rz_out, rr_out};
+    V *X = reinterpret_cast<V *>(S.X), *R = reinterpret_cast<V *>(S.R);
+    const V *P = reinterpret_cast<const V *>(S.P), *Q = reinterpret_cast<const V *>(S.Q);
+    const bool f64 = sizeof(TX) == 8;
+    constexpr int RU4 = 2;  // rows in flight per thread
+    for (int64_t rb = r0 + grp; rb < r1; rb += (int64_t)RU4 * ngrp) {
+        V xv[RU4], rv[RU4], pv[RU4], qv[RU4];
+        TX dd[RU4];
+#pragma unroll
+        for (int t = 0; t < RU4; ++t) {
+            const int64_t r = rb + (int64_t)t * ngrp;
+            if (r < r1) {
+                const int64_t e = r * kv + jv;
+                dd[t] = f64 ? (TX)S.A.dinv[r] : (TX)S.A.dinv32[r];
+                xv[t] = X[e]; rv[t] = R[e]; pv[t] = P[e]; qv[t] = Q[e];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RU4; ++t) {
+            const int64_t r = rb + (int64_t)t * ngrp;
+            if (r < r1) {
+                const int64_t e = r * kv + jv;
+                TX *x = reinterpret_cast<TX *>(&xv[t]), *rr_ = reinterpret_cast<TX *>(&rv[t]);
+                const TX *pp = reinterpret_cast<const TX *>(&pv[t]), *qq = reinterpret_cast<const TX *>(&qv[t]);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {  // frozen columns keep their values (alpha 0)
+                    x[u] += alpha[u] * pp[u];
+                    rr_[u] -= alpha[u] * qq[u];
+                    rz[u] += rr_[u] * (dd[t] * rr_[u]);
+                    rr[u] += rr_[u] * rr_[u];
+                }
+                X[e] = xv[t];
+                R[e] = rv[t];
+            }
+        }
+    }
+}
+
+// per-column block sums of lane partials (VW per lane) in a fixed order
+__device__ __forceinline__ double col_lane_sum(const double *vals, int VW, int k, double *csum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kv = k / VW;
+    int gw = 1;
+    while (gw < kv) gw <<= 1;
+    const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NT / 32 * KMAX; i += NT) csum[i] = 0.0;
+    __syncthreads();
+    for (int g = 0; g < gpw; ++g) {
+        if (grp == g && jv < kv)
+            for (int u = 0; u < VW; ++u) csum[warp * KMAX + jv * VW + u] += vals[u];
+        __syncwarp();
+    }
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < (unsigned)k)
+        for (int w = 0; w < NT / 32; ++w) t += csum[w * KMAX + threadIdx.x];
+    return t;
+}
+
 template <class TX>
-__global__ void __launch_bounds__(NT) k_bupdate(BSys *sys, const int *unit_sys, BGlobal *G, double *partials) {
+__global__ void __launch_bounds__(NT, 4) k_bupdate(BSys *sys, const int *unit_sys, BGlobal *G, double *partials) {
     if (G->done) return;
     __shared__ double sm[NT];
+    __shared__ double csum[NT / 32 * KMAX];
     const int s = unit_sys[blockIdx.x];
     BSys &S = sys[s];
     if (S.active == 0) return;
     const int k = S.k, kw = S.kw;
-    const int j = threadIdx.x % kw, grp = threadIdx.x / kw, ngrp = NT / kw;
-    const bool on = j < k && !S.c.done[j];
-    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
-    const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
-    TX *X = (TX *)S.X, *R = (TX *)S.R;
-    const TX *P = (const TX *)S.P, *Q = (const TX *)S.Q;
-    const bool f64 = sizeof(TX) == 8;
-    TX rz = TX(0), rr = TX(0);
-    if (on) {
-        const TX alpha = (TX)S.c.alpha[j];
-        for (int64_t r = r0 + grp; r < r1; r += ngrp) {
-            const int64_t e = r * k + j;
-            const TX d = f64 ? (TX)S.A.dinv[r] : (TX)S.A.dinv32[r];
-            const TX xi = X[e] + alpha * P[e];
-            const TX ri = R[e] - alpha * Q[e];
-            X[e] = xi;
-            R[e] = ri;
-            rz += ri * (d * ri);
-            rr += ri * ri;
-        }
-    }
-    const double a = col_block_sum((double)rz, sm, kw);
+    const int VW = vec_width<TX>(k);
+    double rz[4] = {0, 0, 0, 0}, rr[4] = {0, 0, 0, 0};
+    if (VW == 4) bupdate_rows<TX, (sizeof(TX) == 4 ? 4 : 2)>(S, k, rz, rr);
+    else if (VW == 2) bupdate_rows<TX, 2>(S, k, rz, rr);
+    else bupdate_rows<TX, 1>(S, k, rz, rr);
+    const double a = col_lane_sum(rz, VW, k, csum);
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = a;
-    const double b = col_block_sum((double)rr, sm, kw);
+    const double b = col_lane_sum(rr, VW, k, csum);
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2 + 1) * KMAX + threadIdx.x] = b;
     if (sys_arrive_last(&S.ticket, S.nunits)) {
+        const double rz_t = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
+        const double rr_t = col_unit_sum_block(partials, S.unit0, S.nunits, 1, 2, kw, sm);
         if (threadIdx.x < (unsigned)k && !S.c.done[threadIdx.x]) {
             const int jj = threadIdx.x;
-            const double rz_t = col_unit_sum(partials, S.unit0, S.nunits, jj, 0);
-            const double rr_t = col_unit_sum(partials, S.unit0, S.nunits, jj, 1);
             S.c.it[jj] += 1;
             S.c.rr[jj] = rr_t;
             if (!isfinite(rz_t) || !isfinite(rr_t)) { S.c.status[jj] = ST_BREAK; S.c.done[jj] = 1; }
@@ -224,6 +408,58 @@ __global__ void __launch_bounds__(NT) k_bupdate(BSys *sys, const int *unit_sys, 
     }
 }
 
+template <class TX, int VW>
+__device__ __forceinline__ void bpupdate_rows(BSys &S, int k) {
+    using V = typename VecN<TX, VW>::T;
+    const int kv = k / VW;
+    int gw = 1;
+    while (gw < kv) gw <<= 1;
+    const int jv = (threadIdx.x & 31) % gw, grp = threadIdx.x / gw, ngrp = NT / gw;
+    if (jv >= kv) return;
+    TX beta[VW];
+    bool on[VW];
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+        on[u] = !S.c.done[jv * VW + u];
+        beta[u] = (TX)S.c.beta[jv * VW + u];
+        any |= on[u];
+    }
+    if (!any) return;
+    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
+    const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
+    V *P = reinterpret_cast<V *>(S.P);
+    const V *R = reinterpret_cast<const V *>(S.R);
+    const bool f64 = sizeof(TX) == 8;
+    constexpr int RU4 = 4;  // rows in flight per thread
+    for (int64_t rb = r0 + grp; rb < r1; rb += (int64_t)RU4 * ngrp) {
+        V pv[RU4], rv[RU4];
+        TX dd[RU4];
+#pragma unroll
+        for (int t = 0; t < RU4; ++t) {
+            const int64_t r = rb + (int64_t)t * ngrp;
+            if (r < r1) {
+                const int64_t e = r * kv + jv;
+                dd[t] = f64 ? (TX)S.A.dinv[r] : (TX)S.A.dinv32[r];
+                pv[t] = P[e];
+                rv[t] = R[e];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RU4; ++t) {
+            const int64_t r = rb + (int64_t)t * ngrp;
+            if (r < r1) {
+                TX *pp = reinterpret_cast<TX *>(&pv[t]);
+                const TX *rp = reinterpret_cast<const TX *>(&rv[t]);
+#pragma unroll
+                for (int u = 0; u < VW; ++u)
+                    if (on[u]) pp[u] = dd[t] * rp[u] + beta[u] * pp[u];
+                P[r * kv + jv] = pv[t];
+            }
+        }
+    }
+}
+
 // P = D^-1 R + beta P for the active columns; the block that ends the
 // iteration last applies a pending stop (retirement, budget, all done), so a
 // loop only ever stops between complete iterations.
@@ -232,20 +468,12 @@ __global__ void __launch_bounds__(NT) k_bpupdate(BSys *sys, const int *unit_sys,
     if (G->done) return;
     const int s = unit_sys[blockIdx.x];
     BSys &S = sys[s];
-    const int k = S.k, kw = S.kw;
-    const int j = threadIdx.x % kw, grp = threadIdx.x / kw, ngrp = NT / kw;
-    if (S.active != 0 && j < k && !S.c.done[j]) {
-        const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
-        const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
-        TX *P = (TX *)S.P;
-        const TX *R = (const TX *)S.R;
-        const TX beta = (TX)S.c.beta[j];
-        const bool f64 = sizeof(TX) == 8;
-        for (int64_t r = r0 + grp; r < r1; r += ngrp) {
-            const int64_t e = r * k + j;
-            const TX d = f64 ? (TX)S.A.dinv[r] : (TX)S.A.dinv32[r];
-            P[e] = d * R[e] + beta * P[e];
-        }
+    const int k = S.k;
+    if (S.active != 0) {
+        const int VW = vec_width<TX>(k);
+        if (VW == 4) bpupdate_rows<TX, (sizeof(TX) == 4 ? 4 : 2)>(S, k);
+        else if (VW == 2) bpupdate_rows<TX, 2>(S, k);
+        else bpupdate_rows<TX, 1>(S, k);
     }
     __shared__ bool last;
     __threadfence();
@@ -288,10 +516,10 @@ __global__ void __launch_bounds__(NT) k_bstart(BSys *sys, const int *unit_sys, d
     const double a = col_block_sum(rz, sm, kw);
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = a;
     if (sys_arrive_last(&S.ticket, S.nunits)) {
+        const double t = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
         if (threadIdx.x < (unsigned)k) {
             const int jj = threadIdx.x;
             if (mask[s * KMAX + jj]) {
-                const double t = col_unit_sum(partials, S.unit0, S.nunits, jj, 0);
                 S.c.rho[jj] = t;
                 S.c.done[jj] = 0;
                 S.c.status[jj] = ST_RUN;
@@ -346,13 +574,14 @@ static __global__ void __launch_bounds__(NT) k_bresid(BSys *sys, const int *unit
     const double b = col_block_sum(bb, sm, kw);
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2 + 1) * KMAX + threadIdx.x] = b;
     if (sys_arrive_last(&S.ticket, S.nunits)) {
+        const double rr_t = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
+        const double bb_t = col_unit_sum_block(partials, S.unit0, S.nunits, 1, 2, kw, sm);
         if (threadIdx.x < (unsigned)k) {
             const int jj = threadIdx.x;
-            S.c.rr[jj] = col_unit_sum(partials, S.unit0, S.nunits, jj, 0);
+            S.c.rr[jj] = rr_t;
             if (init) {
-                const double bt = col_unit_sum(partials, S.unit0, S.nunits, jj, 1);
-                S.c.bb[jj] = bt;
-                S.c.thresh[jj] = tol * tol * bt;
+                S.c.bb[jj] = bb_t;
+                S.c.thresh[jj] = tol * tol * bb_t;
             }
         }
         __syncthreads();
@@ -429,17 +658,13 @@ static __global__ void __launch_bounds__(NT) k_breplace(BSys *sys, const int *un
     const double c = col_block_sum(rp, sm, kw);
     if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 3 + 2) * KMAX + threadIdx.x] = c;
     if (sys_arrive_last(&S.ticket, S.nunits)) {
+        const double rz_t = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 3, kw, sm);
+        const double rr_t = col_unit_sum_block(partials, S.unit0, S.nunits, 1, 3, kw, sm);
+        const double rp_t = col_unit_sum_block(partials, S.unit0, S.nunits, 2, 3, kw, sm);
         if (threadIdx.x < (unsigned)k) {
             const int jj = threadIdx.x;
             const int mm = mask[s * KMAX + jj];
             if (mm) {
-                double rz_t = 0.0, rr_t = 0.0, rp_t = 0.0;
-                for (int u = 0; u < S.nunits; ++u) {
-                    const size_t base = (size_t)(S.unit0 + u) * 3;
-                    rz_t += __ldcg(partials + (base + 0) * KMAX + jj);
-                    rr_t += __ldcg(partials + (base + 1) * KMAX + jj);
-                    rp_t += __ldcg(partials + (base + 2) * KMAX + jj);
-                }
                 if (mm == 1 && rz_t > 0.0 && S.c.rho[jj] > 0.0) {
                     const double beta = rz_t / S.c.rho[jj];
                     S.c.beta[jj] = beta;
