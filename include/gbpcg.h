@@ -173,6 +173,27 @@ int sell_info(const gb_sell *A, gb_sell_info *out);
 int sell_spmv(const gb_sell *A, const double *d_x, double *d_y, void *stream);
 void sell_destroy(gb_sell *A);
 
+/* Autotuner: builds the matrix in each candidate layout -- chunk height C
+ * (32, 64, 128), sorting window sigma (64, 256, 1024), SpMV variant (TMA-
+ * staged streams or one row per lane) -- times a CG iteration of each for
+ * `precision` (GB_F64, GB_F32_IR or GB_BF16_IR; d_b: a right-hand side, n
+ * doubles, original order) with CUDA events, and returns the fastest in
+ * *best.  With out != NULL the winning matrix is returned (its SpMV variant
+ * becomes the default of later solves on it), else it is destroyed.
+ * Synchronises `stream`. */
+typedef struct SellTuneResult {
+    int32_t C, sigma, spmv_variant, candidates;
+    double iter_ms;   /* one CG iteration of the winner (sum of its three kernels) */
+    double spmv_ms;   /* its SpMV + p.q kernel */
+} SellTuneResult;
+int sell_autotune(const gb_fem_system *sys, const double *d_b, int precision, int val_types,
+                  const gb_allocator *alloc, void *stream, SellTuneResult *best, gb_sell **out);
+/* Sets the SpMV variant later solves on A use when PcgOptions.spmv_variant is
+ * 0 (the autotuner's choice, replayed from a cache): 0 = TMA-staged streams
+ * where the layout has them (C = 32), 1 = one row per lane.  GB_EINVAL for
+ * another value. */
+int sell_set_variant(gb_sell *A, int variant);
+
 /* ------------------------------------------------------------------ PCG --
  * Jacobi-PCG: r = b - A x0, z = D^{-1} r, p = z; iterate q = A p,
  * alpha = r.z / p.q, x += alpha p, r -= alpha q, z = D^{-1} r, beta = r.z'/r.z,

@@ -122,6 +122,30 @@ class FemSystem:
         return Sell(h, stream if stream is not None else self._stream)
 
 
+_TUNED = {}  # mesh spec + precision -> chosen (C, sigma, variant)
+
+
+def autotune(system, b, precision=G.GB_F64, val_types=G.GB_VAL_F64 | G.GB_VAL_F32, stream=None):
+    """sell_autotune: (Sell in the fastest layout, result dict).  The choice
+    is cached per mesh spec and precision; a cached spec builds that layout
+    directly."""
+    spec = system.spec
+    key = (spec.dim, spec.degree, spec.cells, spec.jitter, spec.diag_mode, spec.seed, precision, val_types)
+    if key in _TUNED:
+        cfg = _TUNED[key]
+        A = system.to_sell(cfg["C"], cfg["sigma"], val_types, stream=stream)
+        G.check(G.lib().sell_set_variant(A.handle, cfg["spmv_variant"]), "sell_set_variant")
+        return A, dict(cfg, cached=True)
+    res = G.SellTuneResult()
+    h = C.c_void_p()
+    G.check(G.lib().sell_autotune(system.handle, G.ptr(b.contiguous().reshape(-1)), precision, val_types,
+                                  G.torch_allocator(), G.stream_ptr(stream), C.byref(res), C.byref(h)),
+            "sell_autotune")
+    cfg = res.as_dict()
+    _TUNED[key] = cfg
+    return Sell(h, stream), dict(cfg, cached=False)
+
+
 class Sell:
     """A SELL-C-sigma matrix (csr_to_sell / csr_to_sell_raw)."""
 

@@ -614,7 +614,7 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
         GB_CHECK_CUDA(cudaGetLastError());
         auto body = [&](cudaStream_t s) {
             enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.partials, w.S, g, s,
-                                                      o.spmv_variant);
+                                                      o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr));
         GB_TRY(read_scal(w.S, &h, st));
@@ -687,7 +687,7 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         launches += 2;
         auto body = [&](cudaStream_t s) {
             enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
-                                                o.spmv_variant);
+                                                o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
         PcgScal hi{};
@@ -790,7 +790,7 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         const long long it0 = hr.it;
         auto body = [&](cudaStream_t s) {
             enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
-                                                o.spmv_variant);
+                                                o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
         PcgScal hi{};
@@ -901,8 +901,8 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     return GB_OK;
 }
 
-extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters,
-                                void *stream, double *h_ms) {
+static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision, int iters, int variant,
+                             void *stream, double *h_ms) {
     GB_REQUIRE(A && d_b && h_ms, "pcg_kernel_times: NULL argument");
     GB_REQUIRE(iters >= 1 && iters <= 100000, "pcg_kernel_times: iters must be in 1..100000");
     GB_REQUIRE(precision >= GB_F64 && precision <= GB_BF16_IR, "pcg_kernel_times: bad precision");
@@ -945,7 +945,7 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
     cudaEventRecord(ev[0], st);
     for (int i = 0; i < iters; ++i) {
         for (int k = 0; k < 3; ++k) {
-            if (k == 0 && A->C == 32 && A->warp_chunk) {
+            if (k == 0 && A->C == 32 && A->warp_chunk && variant == 0) {
                 if (precision == GB_F64) launch_spmv_tma<double, double>(V, A->val, w.p, w.q, w.partials, w.S, st);
                 else if (precision == GB_F32_IR) launch_spmv_tma<float, float>(V, A->val32, w.p32, w.q32, w.partials, w.S, st);
                 else launch_spmv_tma<__nv_bfloat16, float>(V, A->val16, w.p32, w.q32, w.partials, w.S, st);
@@ -1005,6 +1005,63 @@ extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precisi
     }
     for (int k = 0; k < 3; ++k) h_ms[k] = tot[k] / iters;
     return rc;
+}
+
+extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters,
+                                void *stream, double *h_ms) {
+    GB_REQUIRE(A, "pcg_kernel_times: NULL matrix");
+    return kernel_times_impl(A, d_b, precision, iters, A->variant_hint, stream, h_ms);
+}
+
+extern "C" int sell_set_variant(gb_sell *A, int variant) {
+    GB_REQUIRE(A, "sell_set_variant: NULL matrix");
+    GB_REQUIRE(variant == 0 || variant == 1, "sell_set_variant: variant must be 0 or 1");
+    A->variant_hint = variant;
+    return GB_OK;
+}
+
+// ---------------------------------------------------------------- autotune --
+// Times one CG iteration (SpMV + p.q, x/r update, p update) of every candidate
+// layout (chunk height C, sorting window sigma, SpMV variant) on this matrix
+// and precision, and keeps the fastest.  The winner's variant is recorded in
+// the matrix, so later solves use it without being told.
+extern "C" int sell_autotune(const gb_fem_system *sys, const double *d_b, int precision, int val_types,
+                             const gb_allocator *alloc, void *stream, SellTuneResult *best, gb_sell **out) {
+    GB_REQUIRE(sys && d_b && best, "sell_autotune: NULL argument");
+    GB_REQUIRE(precision == GB_F64 || precision == GB_F32_IR || precision == GB_BF16_IR,
+               "sell_autotune: precision must be GB_F64, GB_F32_IR or GB_BF16_IR");
+    struct Cand { int C, sigma, variant; };
+    static const Cand cands[] = {{32, 256, 0}, {32, 64, 0}, {32, 1024, 0}, {32, 256, 1},
+                                 {64, 256, 1}, {128, 256, 1}, {64, 1024, 1}};
+    *best = SellTuneResult{};
+    best->iter_ms = 1e300;
+    gb_sell *keep = nullptr;
+    int rc = GB_OK;
+    for (const Cand &c : cands) {
+        gb_sell *A = nullptr;
+        rc = csr_to_sell(sys, c.C, c.sigma, val_types, alloc, stream, &A);
+        if (rc != GB_OK) break;
+        if (c.variant == 0 && !A->warp_chunk) { sell_destroy(A); continue; }
+        double ms[3] = {0, 0, 0};
+        rc = kernel_times_impl(A, d_b, precision, 2, c.variant, stream, ms);  // warm-up
+        if (rc == GB_OK) rc = kernel_times_impl(A, d_b, precision, 8, c.variant, stream, ms);
+        if (rc != GB_OK) { sell_destroy(A); break; }
+        const double it = ms[0] + ms[1] + ms[2];
+        if (it < best->iter_ms) {
+            best->C = c.C; best->sigma = c.sigma; best->spmv_variant = c.variant;
+            best->iter_ms = it; best->spmv_ms = ms[0];
+            A->variant_hint = c.variant;
+            if (keep) sell_destroy(keep);
+            keep = A;
+        } else {
+            sell_destroy(A);
+        }
+        best->candidates += 1;
+    }
+    if (rc != GB_OK) { if (keep) sell_destroy(keep); return rc; }
+    if (out) *out = keep;
+    else if (keep) sell_destroy(keep);
+    return GB_OK;
 }
 
 // ------------------------------------------------------- no-allocation solve --

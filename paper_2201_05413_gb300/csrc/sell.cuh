@@ -33,6 +33,7 @@ struct gb_sell {
     int32_t *warp_chunk = nullptr;
     int16_t *col16 = nullptr;
     int nwarps = 0;
+    int variant_hint = 0;  // SpMV variant solves use by default (set by sell_autotune)
     int64_t *chunk_ptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
     float *val32 = nullptr, *dinv32 = nullptr;

@@ -74,6 +74,14 @@ class PcgStats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class SellTuneResult(C.Structure):
+    _fields_ = [("C", C.c_int32), ("sigma", C.c_int32), ("spmv_variant", C.c_int32),
+                ("candidates", C.c_int32), ("iter_ms", C.c_double), ("spmv_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class ServeOptions(C.Structure):
     _fields_ = [("mem_budget", C.c_size_t), ("max_slots", C.c_int32), ("precision", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int64), ("iters_per_step", C.c_int32),
@@ -121,6 +129,9 @@ _SIGS = {
     "csr_to_sell_raw": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int, C.c_int, C.c_int,
                                   C.POINTER(gb_allocator), _P, C.POINTER(_P)]),
     "sell_info": (C.c_int, [_P, C.POINTER(gb_sell_info)]),
+    "sell_autotune": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(gb_allocator), _P,
+                                C.POINTER(SellTuneResult), C.POINTER(_P)]),
+    "sell_set_variant": (C.c_int, [_P, C.c_int]),
     "sell_spmv": (C.c_int, [_P, _P, _P, _P]),
     "sell_destroy": (None, [_P]),
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
