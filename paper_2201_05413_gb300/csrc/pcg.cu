@@ -77,7 +77,61 @@ static void launch_spmv_tma_t(const SellView &A, const TV *val, const TX *p, TX 
     ::gb::count_launches(1); k_spmv_tma<TV, TX, TI><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
 }
 
-// 16-bit column deltas when the matrix has them, 32-bit indices otherwise
+// q = A p with the second streaming loop (32-bit indices, spmv_tma.cuh), one
+// warp per balanced chunk range, then the p.q reduction and alpha.
+template <class TV, class TX>
+__global__ void __launch_bounds__(NT) k_spmv_tma2(SellView A, const TV *__restrict__ val,
+                                                  const TX *__restrict__ p, TX *__restrict__ q,
+                                                  double *partials, PcgScal *S) {
+    if (S->done) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && S->use_cond) cudaGraphSetConditional(S->cond, 0);
+        return;
+    }
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ double sm[NT / 32];
+    constexpr int NB = Tma2Cfg<TV>::NB;
+    Tma2Ring<TV> *bufs = reinterpret_cast<Tma2Ring<TV> *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + TMA_WARPS * sizeof(Tma2Ring<TV>));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        for (int b = 0; b < NB; ++b) mbar_init(&bars[NB * warp + b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncwarp();
+    const int gw = blockIdx.x * TMA_WARPS + warp;
+    const int c0 = __ldg(A.warp_chunk + gw), c1 = __ldg(A.warp_chunk + gw + 1);
+    bool timed_out = false;
+    const TX dot = spmv_warp_stream2<TV, TX>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
+    if (timed_out && lane == 0) atomicExch(&S->err, 1);
+    const double t = block_sum<NT>((double)dot, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (arrive_last(&S->ticket)) {
+        const double pq = sum_partials(partials, gridDim.x, 1, 0, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->pq = pq;
+            if (S->err) stop(S, ST_TIMEOUT);
+            else if (!(pq > 0.0) || !isfinite(pq)) stop(S, ST_BREAK);
+            else S->alpha = S->rho / pq;
+        }
+    }
+}
+
+template <class TV, class TX>
+static void launch_spmv_tma2(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+                             PcgScal *S, cudaStream_t st) {
+    static bool attr_set = false;  // per instantiation
+    const int smem = (int)tma2_smem_bytes<TV>();
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_spmv_tma2<TV, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    ::gb::count_launches(1); k_spmv_tma2<TV, TX><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+}
+
+// 16-bit column deltas when the matrix has them (first streaming loop), 32-bit
+// indices otherwise (second streaming loop)
 template <class TV, class TX>
 static void launch_spmv_tma(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
                             PcgScal *S, cudaStream_t st) {
@@ -85,7 +139,11 @@ static void launch_spmv_tma(const SellView &A, const TV *val, const TX *p, TX *q
     if (A.col16) launch_spmv_tma_t<TV, TX, int16_t>(A, val, p, q, partials, S, st);
     else
 #endif
+#ifdef GB_TMA_OLD
         launch_spmv_tma_t<TV, TX, int32_t>(A, val, p, q, partials, S, st);
+#else
+        launch_spmv_tma2<TV, TX>(A, val, p, q, partials, S, st);
+#endif
 }
 
 // ------------------------------------------------------------ kernels --
@@ -148,13 +206,35 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
     }
 }
 
-template <class TX> struct Vec2;
-template <> struct Vec2<double> { using T = double2; };
-template <> struct Vec2<float> { using T = float2; };
+// 16-byte accesses of the streaming vector kernels: VW elements of T per load
+// (4 fp32 / 2 fp64); a type narrower than the step's element count (fp32
+// D^-1 beside fp64 vectors) takes fewer bytes per access.
+template <class T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
+template <class T, int N>
+__device__ __forceinline__ void ld_pack(const T *p, int64_t i, T (&o)[N]) {
+    if constexpr (sizeof(T) * N <= 16) {
+        const Pack<T, N> v = reinterpret_cast<const Pack<T, N> *>(p)[i];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = v.v[k];
+    } else {
+        constexpr int H = N / 2;
+        const Pack<T, H> a = reinterpret_cast<const Pack<T, H> *>(p)[2 * i];
+        const Pack<T, H> b = reinterpret_cast<const Pack<T, H> *>(p)[2 * i + 1];
+#pragma unroll
+        for (int k = 0; k < H; ++k) { o[k] = a.v[k]; o[H + k] = b.v[k]; }
+    }
+}
+template <class T, int N>
+__device__ __forceinline__ void st_pack(T *p, int64_t i, const T (&o)[N]) {
+    Pack<T, N> v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v.v[k] = o[k];
+    reinterpret_cast<Pack<T, N> *>(p)[i] = v;
+}
 
-// Grid-stride over element pairs, UPD_U pairs per thread per step with every
+// Grid-stride over 16-byte groups, UPD_U groups per thread per step with every
 // load issued before the arithmetic (memory-level parallelism for these
-// streaming kernels); the odd last element, if any, goes to thread 0.
+// streaming kernels); the n % VW last elements go to block 0.
 #ifndef GB_UPD_U
 #define GB_UPD_U 2
 #endif
@@ -167,45 +247,43 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
                                                PcgScal *S) {
     if (S->done) return;
     __shared__ double sm[NT / 32];
-    using V2 = typename Vec2<TX>::T;
-    using D2 = typename Vec2<TD>::T;
+    constexpr int VW = 16 / sizeof(TX);
     const TX alpha = (TX)S->alpha;
     TX rz = TX(0), rr = TX(0);
-    const int64_t npair = n >> 1;
+    const int64_t ng = n / VW;
     const int64_t stride = (int64_t)gridDim.x * NT;
-    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < npair; i0 += stride * UPD_U) {
-        V2 xv[UPD_U], rv[UPD_U], pv[UPD_U], qv[UPD_U];
-        D2 dv[UPD_U];
+    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < ng; i0 += stride * UPD_U) {
+        TX xv[UPD_U][VW], rv[UPD_U][VW], pv[UPD_U][VW], qv[UPD_U][VW];
+        TD dv[UPD_U][VW];
 #pragma unroll
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < npair) {
-                xv[u] = reinterpret_cast<V2 *>(x)[i];
-                rv[u] = reinterpret_cast<V2 *>(r)[i];
-                pv[u] = reinterpret_cast<const V2 *>(p)[i];
-                qv[u] = reinterpret_cast<const V2 *>(q)[i];
-                dv[u] = reinterpret_cast<const D2 *>(dinv)[i];
+            if (i < ng) {
+                ld_pack(x, i, xv[u]);
+                ld_pack(r, i, rv[u]);
+                ld_pack(p, i, pv[u]);
+                ld_pack(q, i, qv[u]);
+                ld_pack(dinv, i, dv[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < npair) {
-                xv[u].x += alpha * pv[u].x;
-                xv[u].y += alpha * pv[u].y;
-                rv[u].x -= alpha * qv[u].x;
-                rv[u].y -= alpha * qv[u].y;
-                reinterpret_cast<V2 *>(x)[i] = xv[u];
-                reinterpret_cast<V2 *>(r)[i] = rv[u];
-                rz += rv[u].x * ((TX)dv[u].x * rv[u].x);
-                rz += rv[u].y * ((TX)dv[u].y * rv[u].y);
-                rr += rv[u].x * rv[u].x;
-                rr += rv[u].y * rv[u].y;
+            if (i < ng) {
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    xv[u][k] += alpha * pv[u][k];
+                    rv[u][k] -= alpha * qv[u][k];
+                    rz += rv[u][k] * ((TX)dv[u][k] * rv[u][k]);
+                    rr += rv[u][k] * rv[u][k];
+                }
+                st_pack(x, i, xv[u]);
+                st_pack(r, i, rv[u]);
             }
         }
     }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const int64_t i = n - 1;
+    if (blockIdx.x == 0 && threadIdx.x < n - ng * VW) {
+        const int64_t i = ng * VW + threadIdx.x;
         const TX xi = x[i] + alpha * p[i];
         const TX ri = r[i] - alpha * q[i];
         x[i] = xi;
@@ -241,34 +319,36 @@ template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, const TX *__restrict__ r,
                                                 const TD *__restrict__ dinv, const PcgScal *S) {
     if (S->done) return;
-    using V2 = typename Vec2<TX>::T;
-    using D2 = typename Vec2<TD>::T;
+    constexpr int VW = 16 / sizeof(TX);
     const TX beta = (TX)S->beta;
-    const int64_t npair = n >> 1;
+    const int64_t ng = n / VW;
     const int64_t stride = (int64_t)gridDim.x * NT;
-    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < npair; i0 += stride * UPD_U) {
-        V2 pv[UPD_U], rv[UPD_U];
-        D2 dv[UPD_U];
+    for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < ng; i0 += stride * UPD_U) {
+        TX pv[UPD_U][VW], rv[UPD_U][VW];
+        TD dv[UPD_U][VW];
 #pragma unroll
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < npair) {
-                pv[u] = reinterpret_cast<V2 *>(p)[i];
-                rv[u] = reinterpret_cast<const V2 *>(r)[i];
-                dv[u] = reinterpret_cast<const D2 *>(dinv)[i];
+            if (i < ng) {
+                ld_pack(p, i, pv[u]);
+                ld_pack(r, i, rv[u]);
+                ld_pack(dinv, i, dv[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < npair) {
-                pv[u].x = (TX)dv[u].x * rv[u].x + beta * pv[u].x;
-                pv[u].y = (TX)dv[u].y * rv[u].y + beta * pv[u].y;
-                reinterpret_cast<V2 *>(p)[i] = pv[u];
+            if (i < ng) {
+#pragma unroll
+                for (int k = 0; k < VW; ++k) pv[u][k] = (TX)dv[u][k] * rv[u][k] + beta * pv[u][k];
+                st_pack(p, i, pv[u]);
             }
         }
     }
-    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = (TX)dinv[n - 1] * r[n - 1] + beta * p[n - 1];
+    if (blockIdx.x == 0 && threadIdx.x < n - ng * VW) {
+        const int64_t i = ng * VW + threadIdx.x;
+        p[i] = (TX)dinv[i] * r[i] + beta * p[i];
+    }
 }
 
 // r = b - A x (fp64, x optional = 0) with ||r||^2 and ||b||^2.  The last block
@@ -424,7 +504,7 @@ __global__ void k_correct(int64_t n, double *x, double s, const float *d) {
 
 // ------------------------------------------------------------- driver --
 struct Grids {
-    int spmv, vec;
+    int spmv, vec, upd;
 };
 static Grids pick_grids(int64_t n, int C) {
     const int sms = num_sms();
@@ -432,6 +512,8 @@ static Grids pick_grids(int64_t n, int C) {
     const int64_t warps = ((n + C - 1) / C) * (C / 32);
     g.spmv = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (warps + 7) / 8));
     g.vec = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (n + 2 * NT * UPD_U - 1) / (2 * NT * UPD_U)));
+    // x/r and p updates: one wave of resident blocks (4 per SM at <= 64 registers)
+    g.upd = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, (n + 2 * NT * UPD_U - 1) / (2 * NT * UPD_U)));
     return g;
 }
 
@@ -445,8 +527,8 @@ static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, 
     case 64: ::gb::count_launches(1); k_spmv_pq<TV, TX, 64><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     default: ::gb::count_launches(1); k_spmv_pq<TV, TX, 128><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     }
-    ::gb::count_launches(1); k_update<TX, TD><<<g.vec, NT, 0, st>>>(A.n, x, r, p, q, dinv, partials, S);
-    ::gb::count_launches(1); k_pupdate<TX, TD><<<g.vec, NT, 0, st>>>(A.n, p, r, dinv, S);
+    ::gb::count_launches(1); k_update<TX, TD><<<g.upd, NT, 0, st>>>(A.n, x, r, p, q, dinv, partials, S);
+    ::gb::count_launches(1); k_pupdate<TX, TD><<<g.upd, NT, 0, st>>>(A.n, p, r, dinv, S);
 }
 
 static void enqueue_residual(const SellView &A, const double *x, const double *b, double *r,
@@ -957,9 +1039,9 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                     default: ::gb::count_launches(1); k_spmv_pq<double, double, 128><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<double, double><<<g.vec, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.partials, w.S);
+                    ::gb::count_launches(1); k_update<double, double><<<g.upd, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.partials, w.S);
                 } else {
-                    ::gb::count_launches(1); k_pupdate<double, double><<<g.vec, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.S);
+                    ::gb::count_launches(1); k_pupdate<double, double><<<g.upd, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.S);
                 }
             } else {
                 if (k == 0) {
@@ -977,9 +1059,9 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                         }
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<float, float><<<g.vec, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, w.partials, w.S);
+                    ::gb::count_launches(1); k_update<float, float><<<g.upd, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, w.partials, w.S);
                 } else {
-                    ::gb::count_launches(1); k_pupdate<float, float><<<g.vec, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, w.S);
+                    ::gb::count_launches(1); k_pupdate<float, float><<<g.upd, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, w.S);
                 }
             }
             cudaEventRecord(ev[3 * (size_t)i + k + 1], st);

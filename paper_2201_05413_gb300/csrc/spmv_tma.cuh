@@ -244,4 +244,159 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
     return dot;
 }
 
+
+// ------------------------------------------------------------------------
+// Second streaming loop (32-bit indices): the per-entry work is one shared-
+// memory index load, one gather of p, one shared-memory value load and one
+// FMA.  No per-lane length test: a padded slot holds value 0 and points at
+// the row itself (or at row 0 past n), so it adds exactly zero.  The chunk
+// widths of the warp's range are held 32 at a time in a register (lane l:
+// chunk cb + l) and broadcast by shuffle when a chunk completes.  The matrix
+// copies carry an L2 evict-first policy: the matrix is read once per
+// iteration and should not push the solver's vectors out of L2.
+#ifndef GB_TMA2_SJ32
+#define GB_TMA2_SJ32 8
+#endif
+#ifndef GB_TMA2_NB32
+#define GB_TMA2_NB32 3
+#endif
+#ifndef GB_TMA2_SJ64
+#define GB_TMA2_SJ64 8
+#endif
+#ifndef GB_TMA2_NB64
+#define GB_TMA2_NB64 2
+#endif
+#ifndef GB_TMA2_EVICT_FIRST
+#define GB_TMA2_EVICT_FIRST 1
+#endif
+
+template <class TV> struct Tma2Cfg {
+    static constexpr int SJ = sizeof(TV) == 8 ? GB_TMA2_SJ64 : GB_TMA2_SJ32;
+    static constexpr int NB = sizeof(TV) == 8 ? GB_TMA2_NB64 : GB_TMA2_NB32;
+};
+
+template <class TV>
+struct Tma2Ring {
+    static constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
+    int32_t col[NB][SJ * 32];
+    TV val[NB][SJ * 32];
+};
+
+template <class TV>
+constexpr size_t tma2_smem_bytes() {
+    return TMA_WARPS * sizeof(Tma2Ring<TV>) + TMA_WARPS * Tma2Cfg<TV>::NB * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_g2s_pol(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                             uint64_t pol) {
+#if GB_TMA2_EVICT_FIRST
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+#else
+    (void)pol;
+    bulk_g2s(dst, src, bytes, bar);
+#endif
+}
+
+template <class TV, class TX>
+__device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__restrict__ val,
+                                                const TX *__restrict__ p, TX *__restrict__ q, int c0, int c1,
+                                                Tma2Ring<TV> &sm, uint64_t *bars, bool *timed_out) {
+    constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    TX dot = TX(0);
+    if (c0 >= c1) return dot;
+    const int64_t e0 = __ldg(A.chunk_ptr + c0), e1 = __ldg(A.chunk_ptr + c1);
+    const int64_t nsteps = (e1 - e0) >> 5;
+    const int64_t nstages = (nsteps + SJ - 1) / SJ;
+    uint64_t pol = 0;
+    if (GB_TMA2_EVICT_FIRST && lane == 0) pol = l2_policy_evict_first();
+    auto issue = [&](int64_t st) {
+        if (lane == 0) {
+            const int b = (int)(st % NB);
+            const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
+            const int64_t off = e0 + st * SJ * 32;
+            const uint32_t bc = (uint32_t)(sj * 32 * sizeof(int32_t));
+            const uint32_t bv = (uint32_t)(sj * 32 * sizeof(TV));
+            mbar_expect_tx(&bars[b], bc + bv);
+            bulk_g2s_pol(sm.col[b], A.col + off, bc, &bars[b], pol);
+            bulk_g2s_pol(sm.val[b], val + off, bv, &bars[b], pol);
+        }
+    };
+    for (int64_t st = 0; st < nstages && st < NB; ++st) issue(st);
+
+    // chunk cursor: current chunk cb + ci, `left` steps of it still to come
+    int cb = c0, ci = -1, left = 0;
+    int wv = (cb + lane < c1) ? __ldg(A.chunk_w + cb + lane) : 0;
+    int64_t r = (int64_t)c0 * 32 + lane - 32;
+    TX pr = TX(0);
+    auto next_chunk = [&]() {
+        do {
+            if (++ci == 32) {
+                cb += 32;
+                ci = 0;
+                wv = (cb + lane < c1) ? __ldg(A.chunk_w + cb + lane) : 0;
+            }
+            left = __shfl_sync(FULL, wv, ci);
+            r += 32;
+            if (left == 0 && cb + ci < c1 && r < A.n) q[r] = TX(0);  // an all-empty chunk
+        } while (left == 0 && cb + ci < c1);
+        pr = (cb + ci < c1 && r < A.n) ? __ldg(p + r) : TX(0);
+    };
+    next_chunk();
+    TX acc = TX(0);
+    auto step = [&](TV v, TX pv) {
+        acc += to_tx<TX>(v) * pv;
+        if (--left == 0) {  // chunk complete (warp-uniform)
+            if (r < A.n) {
+                q[r] = acc;
+                dot += pr * acc;
+            }
+            acc = TX(0);
+            next_chunk();
+        }
+    };
+    int64_t st_fail = -1;
+    for (int64_t st = 0; st < nstages; ++st) {
+        const int b = (int)(st % NB);
+        const uint32_t parity = (uint32_t)((st / NB) & 1);
+        const bool ok = mbar_wait(&bars[b], parity);
+        if (!__all_sync(FULL, ok)) {
+            *timed_out = true;
+            st_fail = st;
+            break;
+        }
+        const int32_t *cs = sm.col[b];
+        const TV *vs = sm.val[b];
+        const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
+        if (sj == SJ) {
+            TX pv[SJ];
+#pragma unroll
+            for (int jj = 0; jj < SJ; ++jj) pv[jj] = __ldg(p + cs[jj * 32 + lane]);
+#pragma unroll
+            for (int jj = 0; jj < SJ; ++jj) step(vs[jj * 32 + lane], pv[jj]);
+        } else {
+            for (int jj = 0; jj < sj; ++jj) step(vs[jj * 32 + lane], __ldg(p + cs[jj * 32 + lane]));
+        }
+        __syncwarp();
+        fence_proxy_async();  // our reads of buffer b precede the next bulk write into it
+        if (st + NB < nstages) issue(st + NB);
+    }
+    if (st_fail >= 0 && lane == 0) {
+        for (int64_t s2 = st_fail; s2 < nstages && s2 < st_fail + NB; ++s2)
+            (void)mbar_wait(&bars[s2 % NB], (uint32_t)((s2 / NB) & 1));
+    }
+    __syncwarp();
+    return dot;
+}
+
 }  // namespace gb
