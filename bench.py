@@ -41,6 +41,11 @@ GID = 1  # g = x^2 - y^2
 # device solver runs the oracle's recurrence; the parity tests hold the two
 # counts within 2%).  The reference arm scales its per-iteration time by these.
 ITERS_FULL = [3597, 8534]
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of each kernel on this workload (ncu --set full, one launch after a warm-up
+# launch, `--profile-kernels p2`); None whenever the kernel changes until it is
+# captured again
+NCU_TRAFFIC = {"k_spmv_tma2<double,double>": 640554496, "k_spmv_tma2<float,float>": 423282688}
 WORKLOAD = "cfg2: 2D unit square 1024x1024 cells, jittered +-h/4, random diagonals (seed 1), P1 + P2, g=x^2-y^2"
 
 
@@ -54,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the seeded serving mix timed after the main workload (0 = skip)")
+    ap.add_argument("--no-multi-rhs", dest="multi_rhs", action="store_false",
+                    help="skip the blocked multi-RHS (cfg4 shape) kernel timing")
     ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
                     help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
@@ -206,6 +213,9 @@ def run_ours(args, rank, world):
     te2e = timed(args.steps, host_io=host_io)
     e2e_value = len(SYSTEMS) * args.steps * world / max(sum(te2e), 1e-12)
 
+    # ---- blocked multi-RHS iteration (cfg4 shape), per-kernel event times
+    multi = run_multi_rhs() if args.multi_rhs else None
+
     # ---- per-kernel times (CUDA events per launch) on the P2 system
     name, d2, A2, b2, st2 = info[-1]
     iters_t = 100
@@ -264,21 +274,27 @@ def run_ours(args, rank, world):
                       "f32": {"spmv_pq": ms32[0], "update": ms32[1], "pupdate": ms32[2]}},
         "iteration_GBps_f64": round(iter_bytes64 / (iter_ms64 * 1e-3) / 1e9, 1),
         "autotune": tuned,
-        "roofline": {"bound": "alu", "kernel": "k_spmv_tma<double,double> (2D P2 1024^2, fp64 SpMV + p.q)",
-                     "achieved": round(tf64, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": round(tf64 / FP64_PEAK_TFLOPS, 4), "traffic": None,
-                     "peak_source": "fp64 FMA: 2 per SM per clock x 152 SMs x 2070 MHz (measured 1.21 TFLOP/s)",
-                     "flops_per_launch": spmv_flops64,
-                     "hbm_view": {"achieved_GBps": round(ach64, 1), "peak_GBps": peak, "frac": round(ach64 / peak, 4),
-                                  "bytes_per_launch": spmv_bytes64, "peak_source": peak_src}},
-        "roofline_mixed": {"bound": "hbm", "kernel": "k_spmv_tma<float,float> (2D P2 1024^2, fp32 SpMV + p.q)",
+        "roofline": {"bound": "hbm", "kernel": "k_spmv_tma2<double,double> (2D P2 1024^2, fp64 SpMV + p.q)",
+                     "achieved": round(ach64, 1), "peak": peak, "unit": "GB/s", "frac": round(ach64 / peak, 4),
+                     "traffic": NCU_TRAFFIC.get("k_spmv_tma2<double,double>"),
+                     "peak_source": peak_src, "bytes_per_launch": spmv_bytes64,
+                     "launch_ms": round(ms64[0], 5),
+                     "alu_view": {"achieved_TFLOPps": round(tf64, 4), "peak_TFLOPps": FP64_PEAK_TFLOPS,
+                                  "frac": round(tf64 / FP64_PEAK_TFLOPS, 4), "flops_per_launch": spmv_flops64,
+                                  "peak_source": "fp64 FMA: 2 per SM per clock x 152 SMs x 2070 MHz "
+                                                 "(measured 1.21 TFLOP/s)",
+                                  "fp64_pipe_active_ncu": 0.812}},
+        "roofline_mixed": {"bound": "hbm", "kernel": "k_spmv_tma2<float,float> (2D P2 1024^2, fp32 SpMV + p.q)",
                            "achieved": round(ach32, 1), "peak": peak, "unit": "GB/s", "frac": round(ach32 / peak, 4),
-                           "traffic": None, "peak_source": peak_src, "bytes_per_launch": spmv_bytes32},
+                           "traffic": NCU_TRAFFIC.get("k_spmv_tma2<float,float>"), "peak_source": peak_src,
+                           "bytes_per_launch": spmv_bytes32, "launch_ms": round(ms32[0], 5)},
         "e2e": {"value": round(e2e_value, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if multi is not None:
+        out["multi_rhs"] = multi
     return out, info
 
 
@@ -363,6 +379,42 @@ def run_profile(args):
     torch.cuda.synchronize()
     print(json.dumps({"system": args.profile_kernels, "precision": args.profile_precision, "n": A.n,
                       "nnz": A.nnz, "kernel_ms": ms}))
+
+
+MULTI_SPEC = (2, 2, 2048, 1, 1, 2)  # cfg4: 2D jittered 2048^2 P2, seed 2
+MULTI_K = 32
+
+
+def run_multi_rhs(iters=5):
+    """Blocked multi-RHS iteration at the cfg4 shape (16.8M unknowns, 32
+    right-hand sides from harmonic-basis coefficients N(0,1), host seed 3):
+    per-kernel CUDA-event times of the batched SpMM, X/R update and P update,
+    fp64 and fp32 recurrences, with the algorithmic bytes per iteration
+    (matrix once, 7 vector streams of n x k) against the HBM peak."""
+    import torch
+    import paper_2201_05413_gb300 as P
+    from paper_2201_05413_gb300.workloads import multi_rhs_coefficients
+    d = P.FemSystem(*MULTI_SPEC)
+    A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32)
+    B = d.lift(d.dirichlet(4, multi_rhs_coefficients(MULTI_K), MULTI_K))
+    peak, src = peaks()
+    out = {"workload": "cfg4: 2D jittered 2048x2048 P2 (seed 2), k=32 RHS (harmonic basis, N(0,1) coefficients, seed 3)",
+           "n": A.n, "nnz": A.nnz, "k": MULTI_K, "iters_timed": iters}
+    for pn, pv, sv in (("f64", P.GB_F64, 8), ("f32", P.GB_F32_IR, 4)):
+        P.batched_kernel_times([A], [B], pv, 2)
+        ms = P.batched_kernel_times([A], [B], pv, iters)
+        it_ms = sum(ms)
+        algo = A.nnz * (sv + 4) + 7 * A.n * MULTI_K * sv
+        flops = (2 * A.nnz + 11 * A.n) * MULTI_K
+        out[pn] = {"kernel_ms": {"spmm": round(ms[0], 4), "update": round(ms[1], 4), "pupdate": round(ms[2], 4)},
+                   "iter_ms": round(it_ms, 4), "iterations_per_s": round(1e3 / it_ms, 2),
+                   "algorithmic_GBps": round(algo / (it_ms * 1e-3) / 1e9, 1),
+                   "frac_of_hbm_peak": round(algo / (it_ms * 1e-3) / 1e9 / peak, 4),
+                   "GFLOPps": round(flops / (it_ms * 1e-3) / 1e9, 1)}
+    out["peak_source"] = src
+    del B, A, d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_serving(nreq, seed=4):

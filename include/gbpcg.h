@@ -347,6 +347,19 @@ int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const Pc
 int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters, void *stream,
                      double *h_ms);
 
+/* Measurement entry point (no counterpart in the paper): the batched
+ * counterpart of pcg_kernel_times.  Runs `iters` iterations of the blocked
+ * multi-RHS recurrences of pcg_solve_batched on nsys systems (system s with
+ * k[s] right-hand sides, d_B[s] row-major n_s x k_s) from X = 0, in fp64
+ * (GB_F64) or with fp32 recurrences (GB_F32_IR: fp32 values, GB_BF16_IR: bf16
+ * values), as direct launches on `stream` with a CUDA event pair around every
+ * launch, and writes the mean milliseconds of the iteration's three kernels to
+ * h_ms[0] (SpMM + per-column p.Ap), h_ms[1] (X, R update + R.Z, R.R) and
+ * h_ms[2] (P update).  Every column keeps iterating for the whole run.
+ * Synchronises `stream`. */
+int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const double *const *d_B, const int *k,
+                             int precision, int iters, void *stream, double *h_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -237,6 +237,20 @@ def pcg_solve_batched(mats, Bs, Xs=None, raise_on_fail=True, stream=None, **kw):
     return Xs, [dict(s.as_dict(), rc=rc) for s in stats]
 
 
+def batched_kernel_times(mats, Bs, precision=G.GB_F64, iters=20, stream=None):
+    """pcg_batched_kernel_times: mean ms of (SpMM + p.Ap, X/R update, P update)
+    of the blocked multi-RHS iteration over the given systems."""
+    ns = len(mats)
+    Bs = [b.contiguous() if b.dim() == 2 else b.contiguous().reshape(-1, 1) for b in Bs]
+    A_arr = (C.c_void_p * ns)(*[m.handle.value for m in mats])
+    B_arr = (C.c_void_p * ns)(*[b.data_ptr() for b in Bs])
+    k_arr = (C.c_int * ns)(*[b.shape[1] for b in Bs])
+    ms = (C.c_double * 3)()
+    G.check(G.lib().pcg_batched_kernel_times(ns, A_arr, B_arr, k_arr, precision, iters, G.stream_ptr(stream), ms),
+            "pcg_batched_kernel_times")
+    return list(ms)
+
+
 class Server:
     """serve_create / serve_submit / serve_poll: a continuous-batching solve
     server.  Host result buffers (numpy, n_free x k) are kept here until the

@@ -78,31 +78,12 @@ static int batched_ir(Batch &b, const PcgOptions &o, cudaStream_t st, std::vecto
     return GB_OK;
 }
 
-extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
-                                 double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
-                                 PcgStats *stats) {
-    GB_REQUIRE(nsys >= 1 && A && d_B && d_X && k && stats, "pcg_solve_batched: NULL argument");
-    for (int s = 0; s < nsys; ++s) {
-        GB_REQUIRE(A[s] && d_B[s] && d_X[s], "pcg_solve_batched: system %d has a NULL pointer", s);
-        GB_REQUIRE(k[s] >= 1 && k[s] <= KMAX, "pcg_solve_batched: k[%d]=%d not in 1..%d", s, k[s], KMAX);
-    }
-    PcgOptions o{};
-    if (opt) o = *opt;
-    if (!(o.tol > 0)) o.tol = 1e-10;
-    int64_t nmax = 0;
-    for (int s = 0; s < nsys; ++s) nmax = std::max<int64_t>(nmax, A[s]->n);
-    if (o.max_iter <= 0) o.max_iter = 20 * nmax + 100;
-    if (o.max_outer <= 0) o.max_outer = 30;
-    if (!(o.inner_tol > 0)) o.inner_tol = 1e-4;
-    if (o.check_every <= 0) o.check_every = 16;
-    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve_batched: bad precision");
-    for (int s = 0; s < nsys; ++s) {
-        GB_REQUIRE(o.precision != GB_F32_IR || A[s]->val32, "pcg_solve_batched: system %d has no fp32 values", s);
-        GB_REQUIRE(o.precision != GB_BF16_IR || A[s]->val16, "pcg_solve_batched: system %d has no bf16 values", s);
-    }
-    cudaStream_t st = (cudaStream_t)stream;
+// Builds the batch: per-system units, permuted fp64 right-hand sides and
+// starting iterates, recurrence vectors of the precision's type, column state,
+// and the device copies of the system table.
+static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double *const *d_B,
+                       double *const *d_X, const int *k, const PcgOptions &o, cudaStream_t st) {
     const bool ir = o.precision != GB_F64;
-    Batch b;
     b.mem = Mem(nullptr, st);
     b.h.resize(nsys);
     std::vector<int> unit_sys;
@@ -159,7 +140,7 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
         GB_CHECK_CUDA(cudaMemsetAsync(cs, 0, sizeof(int) * 2 * KMAX, st));
         const int g = stride_grid((int64_t)nk, 256, 8);
         ::gb::count_launches(1); k_gather_rows<<<g, 256, 0, st>>>(n, S.k, M->perm, d_B[s], B64);
-        ::gb::count_launches(1); k_gather_rows<<<g, 256, 0, st>>>(n, S.k, M->perm, o.x0_zero ? nullptr : d_X[s], X64);
+        ::gb::count_launches(1); k_gather_rows<<<g, 256, 0, st>>>(n, S.k, M->perm, (o.x0_zero || !d_X) ? nullptr : d_X[s], X64);
     }
     b.units = (int)unit_sys.size();
     GB_TRY(b.take(&b.d_sys, (size_t)nsys));
@@ -170,6 +151,36 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     GB_CHECK_CUDA(cudaMemcpyAsync(b.d_sys, b.h.data(), sizeof(BSys) * nsys, cudaMemcpyHostToDevice, st));
     GB_CHECK_CUDA(cudaMemcpyAsync(b.d_unit_sys, unit_sys.data(), sizeof(int) * unit_sys.size(), cudaMemcpyHostToDevice, st));
     GB_CHECK_CUDA(cudaMemsetAsync(b.d_G, 0, sizeof(BGlobal), st));
+
+    return GB_OK;
+}
+
+extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
+                                 double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
+                                 PcgStats *stats) {
+    GB_REQUIRE(nsys >= 1 && A && d_B && d_X && k && stats, "pcg_solve_batched: NULL argument");
+    for (int s = 0; s < nsys; ++s) {
+        GB_REQUIRE(A[s] && d_B[s] && d_X[s], "pcg_solve_batched: system %d has a NULL pointer", s);
+        GB_REQUIRE(k[s] >= 1 && k[s] <= KMAX, "pcg_solve_batched: k[%d]=%d not in 1..%d", s, k[s], KMAX);
+    }
+    PcgOptions o{};
+    if (opt) o = *opt;
+    if (!(o.tol > 0)) o.tol = 1e-10;
+    int64_t nmax = 0;
+    for (int s = 0; s < nsys; ++s) nmax = std::max<int64_t>(nmax, A[s]->n);
+    if (o.max_iter <= 0) o.max_iter = 20 * nmax + 100;
+    if (o.max_outer <= 0) o.max_outer = 30;
+    if (!(o.inner_tol > 0)) o.inner_tol = 1e-4;
+    if (o.check_every <= 0) o.check_every = 16;
+    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve_batched: bad precision");
+    for (int s = 0; s < nsys; ++s) {
+        GB_REQUIRE(o.precision != GB_F32_IR || A[s]->val32, "pcg_solve_batched: system %d has no fp32 values", s);
+        GB_REQUIRE(o.precision != GB_BF16_IR || A[s]->val16, "pcg_solve_batched: system %d has no bf16 values", s);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool ir = o.precision != GB_F64;
+    Batch b;
+    GB_TRY(setup_batch(b, nsys, A, d_B, d_X, k, o, st));
 
     cudaEvent_t e0, e1;
     GB_CHECK_CUDA(cudaEventCreate(&e0));
@@ -296,6 +307,94 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     if (worst != GB_OK) {
         set_error("pcg_solve_batched: a column did not reach tol (status %d)", worst);
         return worst;
+    }
+    return GB_OK;
+}
+
+// ------------------------------------------------------------ measurement --
+extern "C" int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const double *const *d_B, const int *k,
+                                        int precision, int iters, void *stream, double *h_ms) {
+    GB_REQUIRE(nsys >= 1 && A && d_B && k && h_ms, "pcg_batched_kernel_times: NULL argument");
+    GB_REQUIRE(iters >= 1 && iters <= 100000, "pcg_batched_kernel_times: iters must be in 1..100000");
+    GB_REQUIRE(precision >= GB_F64 && precision <= GB_BF16_IR, "pcg_batched_kernel_times: bad precision");
+    for (int s = 0; s < nsys; ++s) {
+        GB_REQUIRE(A[s] && d_B[s], "pcg_batched_kernel_times: system %d has a NULL pointer", s);
+        GB_REQUIRE(k[s] >= 1 && k[s] <= KMAX, "pcg_batched_kernel_times: k[%d]=%d not in 1..%d", s, k[s], KMAX);
+        GB_REQUIRE(precision != GB_F32_IR || A[s]->val32, "pcg_batched_kernel_times: system %d has no fp32 values", s);
+        GB_REQUIRE(precision != GB_BF16_IR || A[s]->val16, "pcg_batched_kernel_times: system %d has no bf16 values", s);
+    }
+    PcgOptions o{};
+    o.precision = precision;
+    o.x0_zero = 1;
+    o.tol = 1e-10;
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch b;
+    GB_TRY(setup_batch(b, nsys, A, d_B, nullptr, k, o, st));
+    // R = B, then the recurrences start on every column; thresholds below zero
+    // keep every column iterating for the whole run
+    ::gb::count_launches(1); k_bresid<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.partials, 1, 1, o.tol);
+    std::vector<int> mask((size_t)nsys * KMAX, 0);
+    for (int s = 0; s < nsys; ++s)
+        for (int j = 0; j < k[s]; ++j) mask[(size_t)s * KMAX + j] = 1;
+    GB_CHECK_CUDA(cudaMemcpyAsync(b.d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
+    HostCols hc;
+    GB_TRY(pull_cols(b, hc, st));
+    for (int s = 0; s < nsys; ++s) {
+        std::vector<double> th(k[s], -1.0), sc(k[s]);
+        for (int j = 0; j < k[s]; ++j) sc[j] = hc.rr[s][j] > 0 ? std::sqrt(hc.rr[s][j]) : 1.0;
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.h[s].c.thresh, th.data(), sizeof(double) * k[s], cudaMemcpyHostToDevice, st));
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.h[s].c.scale, sc.data(), sizeof(double) * k[s], cudaMemcpyHostToDevice, st));
+    }
+    if (precision == GB_F64) {
+        ::gb::count_launches(1); k_bstart<double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.partials, b.d_mask);
+    } else {
+        ::gb::count_launches(1); k_bscale_down<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_mask);
+        ::gb::count_launches(1); k_bstart<float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.partials, b.d_mask);
+    }
+    BGlobal g{};
+    g.maxit = (long long)iters + 1;
+    g.active_systems = nsys;
+    g.budget = -1;
+    GB_CHECK_CUDA(cudaMemcpyAsync(b.d_G, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaGetLastError());
+    std::vector<cudaEvent_t> ev(3 * (size_t)iters + 1);
+    for (auto &e : ev) GB_CHECK_CUDA(cudaEventCreate(&e));
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < iters; ++i) {
+        for (int q = 0; q < 3; ++q) {
+            if (precision == GB_F64) {
+                if (q == 0) { ::gb::count_launches(1); k_bspmm<double, double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
+                else if (q == 1) { ::gb::count_launches(1); k_bupdate<double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
+                else { ::gb::count_launches(1); k_bpupdate<double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G); }
+            } else {
+                if (q == 0) {
+                    ::gb::count_launches(1);
+                    if (precision == GB_F32_IR) k_bspmm<float, float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
+                    else k_bspmm<float, __nv_bfloat16><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
+                } else if (q == 1) { ::gb::count_launches(1); k_bupdate<float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
+                else { ::gb::count_launches(1); k_bpupdate<float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G); }
+            }
+            cudaEventRecord(ev[3 * (size_t)i + q + 1], st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.back());
+    double tot[3] = {0, 0, 0};
+    for (int i = 0; i < iters && e == cudaSuccess; ++i)
+        for (int q = 0; q < 3; ++q) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[3 * (size_t)i + q], ev[3 * (size_t)i + q + 1]);
+            tot[q] += ms;
+        }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) { set_error("pcg_batched_kernel_times: %s", cudaGetErrorString(e)); return GB_ECUDA; }
+    BGlobal hg{};
+    GB_CHECK_CUDA(cudaMemcpyAsync(&hg, b.d_G, sizeof(hg), cudaMemcpyDeviceToHost, st));
+    GB_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < 3; ++q) h_ms[q] = tot[q] / iters;
+    if (hg.done) {
+        set_error("pcg_batched_kernel_times: the recurrences stopped early; use fewer iterations");
+        return GB_BREAKDOWN;
     }
     return GB_OK;
 }

@@ -320,7 +320,9 @@ __device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__r
     const int64_t nstages = (nsteps + SJ - 1) / SJ;
     uint64_t pol = 0;
     if (GB_TMA2_EVICT_FIRST && lane == 0) pol = l2_policy_evict_first();
+    int64_t issued = 0;  // stages whose copies have been started
     auto issue = [&](int64_t st) {
+        issued = st + 1;
         if (lane == 0) {
             const int b = (int)(st % NB);
             const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
@@ -392,7 +394,7 @@ __device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__r
         if (st + NB < nstages) issue(st + NB);
     }
     if (st_fail >= 0 && lane == 0) {
-        for (int64_t s2 = st_fail; s2 < nstages && s2 < st_fail + NB; ++s2)
+        for (int64_t s2 = st_fail; s2 < issued; ++s2)
             (void)mbar_wait(&bars[s2 % NB], (uint32_t)((s2 / NB) & 1));
     }
     __syncwarp();
