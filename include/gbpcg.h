@@ -360,6 +360,16 @@ int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int ite
 int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const double *const *d_B, const int *k,
                              int precision, int iters, void *stream, double *h_ms);
 
+/* Diagnostic entry point (no counterpart in the paper): exercises, on the
+ * GPU, the bounded wait that the library's kernels use on their shared-memory
+ * transaction barriers.  One warp arms a barrier that nothing completes and
+ * waits on it with a limit of limit_ms milliseconds (0 < limit_ms <= 2000); the
+ * wait gives up, the kernel records how long it waited and returns, and the
+ * call returns GB_TIMEOUT -- the status a solve reports when one of its waits
+ * runs out -- with *h_waited_ms set (may be NULL).  The device stays usable
+ * afterwards.  Allocates 16 bytes with cudaMalloc; synchronises `stream`. */
+int gbpcg_wait_selftest(double limit_ms, void *stream, double *h_waited_ms);
+
 #ifdef __cplusplus
 }
 #endif

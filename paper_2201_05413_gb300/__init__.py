@@ -6,9 +6,9 @@ The compute path is the CUDA library ``libgbpcg.so`` (C ABI in
 ``include/gbpcg.h``); this package only marshals arguments to it.
 """
 from . import gbpcg
-from .api import FemSystem, Sell, Server, autotune, batched_kernel_times, pcg_solve_batched
+from .api import FemSystem, Sell, Server, autotune, batched_kernel_times, pcg_solve_batched, wait_selftest
 from .gbpcg import (GB_BF16_IR, GB_BF16_RU, GB_F32_IR, GB_F32_RU, GB_F64, GB_VAL_BF16, GB_VAL_F32, GB_VAL_F64, GbError,
                     load)
 
-__all__ = ["FemSystem", "Sell", "Server", "autotune", "batched_kernel_times", "pcg_solve_batched", "GbError", "load", "gbpcg", "GB_F64",
+__all__ = ["FemSystem", "Sell", "Server", "autotune", "batched_kernel_times", "pcg_solve_batched", "wait_selftest", "GbError", "load", "gbpcg", "GB_F64",
            "GB_F32_IR", "GB_BF16_IR", "GB_F32_RU", "GB_BF16_RU", "GB_VAL_F64", "GB_VAL_F32", "GB_VAL_BF16"]

@@ -251,6 +251,13 @@ def batched_kernel_times(mats, Bs, precision=G.GB_F64, iters=20, stream=None):
     return list(ms)
 
 
+def wait_selftest(limit_ms=20.0, stream=None):
+    """gbpcg_wait_selftest: (status code, milliseconds the bounded wait waited)."""
+    waited = C.c_double(0.0)
+    rc = G.lib().gbpcg_wait_selftest(float(limit_ms), G.stream_ptr(stream), C.byref(waited))
+    return rc, waited.value
+
+
 class Server:
     """serve_create / serve_submit / serve_poll: a continuous-batching solve
     server.  Host result buffers (numpy, n_free x k) are kept here until the

@@ -86,23 +86,35 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
     const bool ir = o.precision != GB_F64;
     b.mem = Mem(nullptr, st);
     b.h.resize(nsys);
+    b.tma = true;
+    for (int s = 0; s < nsys; ++s) b.tma = b.tma && A[s]->C == 32;
+    // unit table: systems in width-class order (a class's units contiguous)
     std::vector<int> unit_sys;
+    b.cls = ClassRanges{};
+    for (int c = 0; c < ClassRanges::N; ++c) {
+        b.cls.base[c] = (int)unit_sys.size();
+        for (int s = 0; s < nsys; ++s) {
+            if (width_class(k[s]) != c) continue;
+            BSys &S = b.h[s];
+            S.unit0 = (int)unit_sys.size();
+            S.nunits = units_of_rows(A[s]->n, &S.rows_per_unit);
+            for (int u = 0; u < S.nunits; ++u) unit_sys.push_back(s);
+        }
+        b.cls.count[c] = (int)unit_sys.size() - b.cls.base[c];
+    }
     for (int s = 0; s < nsys; ++s) {
         BSys &S = b.h[s];
         const gb_sell *M = A[s];
         const int64_t n = M->n;
+        const int unit0 = S.unit0, nunits = S.nunits;
+        const int64_t rpu = S.rows_per_unit;
         S = BSys{};
         S.A = M->view();
         S.k = k[s];
         S.kw = kw_of(k[s]);
-        const int64_t groups = NT / S.kw;
-        int64_t units = (n + groups * 4 - 1) / (groups * 4);
-        units = std::max<int64_t>(1, std::min<int64_t>(units, 2048));
-        S.rows_per_unit = (n + units - 1) / units;
-        units = (n + S.rows_per_unit - 1) / S.rows_per_unit;
-        S.unit0 = (int)unit_sys.size();
-        S.nunits = (int)units;
-        for (int64_t u = 0; u < units; ++u) unit_sys.push_back(s);
+        S.unit0 = unit0;
+        S.nunits = nunits;
+        S.rows_per_unit = rpu;
         const size_t nk = (size_t)n * S.k;
         double *B64, *X64, *R64;
         GB_TRY(b.take(&B64, nk));
@@ -363,14 +375,13 @@ extern "C" int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const
     for (int i = 0; i < iters; ++i) {
         for (int q = 0; q < 3; ++q) {
             if (precision == GB_F64) {
-                if (q == 0) { ::gb::count_launches(1); k_bspmm<double, double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
+                if (q == 0) launch_bspmm<double, double>(b.tma, b.cls, b.units, b.d_sys, b.d_unit_sys, b.d_G, b.partials, st);
                 else if (q == 1) { ::gb::count_launches(1); k_bupdate<double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
                 else { ::gb::count_launches(1); k_bpupdate<double><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G); }
             } else {
                 if (q == 0) {
-                    ::gb::count_launches(1);
-                    if (precision == GB_F32_IR) k_bspmm<float, float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
-                    else k_bspmm<float, __nv_bfloat16><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
+                    if (precision == GB_F32_IR) launch_bspmm<float, float>(b.tma, b.cls, b.units, b.d_sys, b.d_unit_sys, b.d_G, b.partials, st);
+                    else launch_bspmm<float, __nv_bfloat16>(b.tma, b.cls, b.units, b.d_sys, b.d_unit_sys, b.d_G, b.partials, st);
                 } else if (q == 1) { ::gb::count_launches(1); k_bupdate<float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials); }
                 else { ::gb::count_launches(1); k_bpupdate<float><<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_G); }
             }

@@ -6,72 +6,10 @@
 #include <cmath>
 #include <vector>
 
-#include "pcg.cuh"
+#include "bsys.cuh"
+#include "bspmm_tma.cuh"
 
 namespace gb {
-
-constexpr int KMAX = 32;
-
-struct ColState {  // per-column scalars of one system, arrays of length k
-    double *rho, *pq, *alpha, *beta, *rr, *bb, *thresh, *scale;
-    double *pz, *target;  // reliable updates: z-coefficient of the restored p; fp32 residual floor
-    long long *it;
-    int *done, *status;
-};
-
-struct BSys {
-    SellView A;
-    const void *val;  // matrix values of the recurrence's precision
-    void *X, *R, *P, *Q;  // permuted row-major n x k (element type of the recurrence)
-    const double *B64;    // permuted right-hand side (fp64)
-    double *X64, *R64;    // fp64 solution / residual (refinement and fp64 solves)
-    ColState c;
-    int k, kw;
-    int unit0, nunits;
-    int64_t rows_per_unit;
-    unsigned int ticket;
-    int active;  // columns still iterating
-};
-
-struct BGlobal {
-    long long maxit;
-    int active_systems;
-    int done;
-    int use_cond;
-    int stop_req;        // a stop requested during this iteration (applied at its end)
-    int stop_on_retire;  // stop the loop as soon as any system retires (serving)
-    int budget;          // iterations left in this launch sequence; < 0 = unlimited
-    unsigned int ticket; // end-of-iteration counter of k_bpupdate
-    cudaGraphConditionalHandle cond;
-};
-
-__device__ __forceinline__ void bstop_all(BGlobal *G) {
-    G->done = 1;
-    if (G->use_cond) cudaGraphSetConditional(G->cond, 0);
-}
-
-// system's last block: count active columns; a system whose columns are all
-// frozen retires, and the loop is asked to stop at the end of this iteration
-// when it was the last one (or when the caller wants to see every retirement)
-__device__ __forceinline__ void retire_if_idle(BSys &S, BGlobal *G) {
-    int a = 0;
-    for (int j = 0; j < S.k; ++j) a += S.c.done[j] ? 0 : 1;
-    if (S.active > 0 && a == 0) {
-        const int left = atomicSub(&G->active_systems, 1) - 1;
-        if (left == 0 || G->stop_on_retire) G->stop_req = 1;
-    }
-    S.active = a;
-}
-
-__device__ __forceinline__ bool sys_arrive_last(unsigned int *ticket, int nunits) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)nunits - 1;
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
 
 // per-column block reduction: smem[NT] holds one value per thread; column j
 // sums the groups' entries in group order.  Result in threads j < kw.
@@ -83,25 +21,6 @@ __device__ __forceinline__ double col_block_sum(double v, double *smem, int kw) 
     if (threadIdx.x < (unsigned)kw)
         for (int g = 0; g < NT / kw; ++g) s += smem[g * kw + threadIdx.x];
     return s;
-}
-
-// Per-column sum of a system's unit partials by the whole block: thread t
-// sums units t/kw, t/kw + NT/kw, ... of column t%kw, then column j adds the
-// NT/kw part sums in order.  Fixed order: deterministic.  All threads call;
-// the result is valid in threads j < kw.  stride = partial slots per unit.
-__device__ __forceinline__ double col_unit_sum_block(const double *partials, int unit0, int nunits, int slot,
-                                                     int stride, int kw, double *smem) {
-    const int j = threadIdx.x % kw, part = threadIdx.x / kw, nparts = NT / kw;
-    double s = 0.0;
-    for (int u = part; u < nunits; u += nparts) s += __ldcg(partials + ((size_t)(unit0 + u) * stride + slot) * KMAX + j);
-    __syncthreads();
-    smem[threadIdx.x] = s;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < (unsigned)kw)
-        for (int q = 0; q < nparts; ++q) t += smem[q * kw + threadIdx.x];
-    __syncthreads();
-    return t;
 }
 
 template <class T> __device__ __forceinline__ float ldv(const T *p);
@@ -156,7 +75,7 @@ template <class TX> __host__ __device__ __forceinline__ int vec_width(int k) {
 }
 
 template <class TX, class TV, int VW>
-__device__ __forceinline__ void bspmm_rows(BSys &S, int k, double *colsum /* per-lane dot partials, VW */) {
+__device__ __forceinline__ void bspmm_rows(BSys &S, int unit, int k, TX *colsum /* per-lane dot partials, VW */) {
     using V = typename VecN<TX, VW>::T;
     const int kv = k / VW;                 // vector columns
     int gw = 1;
@@ -170,7 +89,7 @@ __device__ __forceinline__ void bspmm_rows(BSys &S, int k, double *colsum /* per
         for (int u = 0; u < VW; ++u) any |= !S.c.done[jv * VW + u];
         on = any;
     }
-    const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
+    const int64_t r0 = (int64_t)(unit - S.unit0) * S.rows_per_unit;
     const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
     const V *P = reinterpret_cast<const V *>(S.P);
     V *Q = reinterpret_cast<V *>(S.Q);
@@ -217,46 +136,65 @@ __device__ __forceinline__ void bspmm_rows(BSys &S, int k, double *colsum /* per
             const V pr = P[r * kv + jv];
             const TX *a = reinterpret_cast<const TX *>(&acc), *b = reinterpret_cast<const TX *>(&pr);
 #pragma unroll
-            for (int u = 0; u < VW; ++u) colsum[u] += (double)(a[u] * b[u]);
+            for (int u = 0; u < VW; ++u) colsum[u] += a[u] * b[u];
         }
     }
 }
 
+// Per-column block sums of lane partials (lane jv = lane % gw owns columns
+// jv*VW .. jv*VW+VW-1): an xor tree over the lanes of a column inside each warp
+// in the recurrence's precision, then the warps in order in fp64.  Fixed
+// order: deterministic.  All threads call; valid in threads j < k.
+template <class TX, int VW>
+__device__ __forceinline__ double col_tree_sum(TX (&v)[VW], int k, double *csum /* NT/32 x KMAX */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kv = k / VW;
+    int gw = 1;
+    while (gw < kv) gw <<= 1;
+    for (int o = gw; o < 32; o <<= 1)
+#pragma unroll
+        for (int u = 0; u < VW; ++u) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+    __syncthreads();  // csum may still be read by a previous call
+    if (lane < kv)
+#pragma unroll
+        for (int u = 0; u < VW; ++u) csum[warp * KMAX + lane * VW + u] = (double)v[u];
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < (unsigned)k)
+        for (int w = 0; w < NT / 32; ++w) t += csum[w * KMAX + threadIdx.x];
+    return t;
+}
+
+template <class TX, class TV, int VW>
+__device__ __forceinline__ void bspmm_block(BSys &S, int unit, int k, double *partials, double *csum) {
+    TX colsum[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) colsum[u] = TX(0);
+    bspmm_rows<TX, TV, VW>(S, unit, k, colsum);
+    const double t = col_tree_sum<TX, VW>(colsum, k, csum);
+    if (threadIdx.x < (unsigned)k) partials[((size_t)unit * 2) * KMAX + threadIdx.x] = t;
+}
+
+// General SpMM (any chunk height): groups of lanes own rows, lanes own VW
+// consecutive columns; over the units [unit_base, unit_base + gridDim.x).
 template <class TX, class TV>
-__global__ void __launch_bounds__(NT, 4) k_bspmm(BSys *sys, const int *unit_sys, BGlobal *G, double *partials) {
+__global__ void __launch_bounds__(NT, 4) k_bspmm(BSys *sys, const int *unit_sys, int unit_base, BGlobal *G,
+                                                 double *partials) {
     if (G->done) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && G->use_cond) cudaGraphSetConditional(G->cond, 0);
         return;
     }
     __shared__ double sm[NT];
     __shared__ double csum[NT / 32 * KMAX];  // per warp, per column
-    const int s = unit_sys[blockIdx.x];
+    const int unit = unit_base + blockIdx.x;
+    const int s = unit_sys[unit];
     BSys &S = sys[s];
     if (S.active == 0) return;
     const int k = S.k, kw = S.kw;
     const int VW = vec_width<TX>(k);
-    double colsum[4] = {0.0, 0.0, 0.0, 0.0};
-    if (VW == 4) bspmm_rows<TX, TV, (sizeof(TX) == 4 ? 4 : 2)>(S, k, colsum);
-    else if (VW == 2) bspmm_rows<TX, TV, 2>(S, k, colsum);
-    else bspmm_rows<TX, TV, 1>(S, k, colsum);
-    // per-column p.q over the block in a fixed order: lanes -> warp slots -> warps
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int kv = k / VW;
-    int gw = 1;
-    while (gw < kv) gw <<= 1;
-    const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
-    for (int i = threadIdx.x; i < NT / 32 * KMAX; i += NT) csum[i] = 0.0;
-    __syncthreads();
-    for (int g = 0; g < gpw; ++g) {  // groups of a warp add in order
-        if (grp == g && jv < kv)
-            for (int u = 0; u < VW; ++u) csum[warp * KMAX + jv * VW + u] += colsum[u];
-        __syncwarp();
-    }
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < (unsigned)k)
-        for (int w = 0; w < NT / 32; ++w) t += csum[w * KMAX + threadIdx.x];
-    if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = t;
+    if (VW == 4) bspmm_block<TX, TV, (sizeof(TX) == 4 ? 4 : 2)>(S, unit, k, partials, csum);
+    else if (VW == 2) bspmm_block<TX, TV, 2>(S, unit, k, partials, csum);
+    else bspmm_block<TX, TV, 1>(S, unit, k, partials, csum);
     if (sys_arrive_last(&S.ticket, S.nunits)) {
         const double pq = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
         if (threadIdx.x < (unsigned)k && !S.c.done[threadIdx.x]) {
@@ -278,10 +216,8 @@ __global__ void __launch_bounds__(NT, 4) k_bspmm(BSys *sys, const int *unit_sys,
 // R.D^-1 R and R.R; lanes own VW consecutive columns of a row (vector loads),
 // groups of lanes own rows.  The system's last block reduces in a fixed order.
 template <class TX, int VW>
-__device__ __forceinline__ void bupdate_rows(BSys &S, int k, double *rz_out, double *rr_out) {
-    TX rz[VW], rr[VW];  // per-lane partial sums in the recurrence's precision
-#pragma unroll
-    for (int u = 0; u < VW; ++u) { rz[u] = TX(0); rr[u] = TX(0); }
+__device__ __forceinline__ void bupdate_rows(BSys &S, int k, TX (&rz)[VW], TX (&rr)[VW]) {
+    // per-lane partial sums in the recurrence's precision (zero on entry)
     using V = typename VecN<TX, VW>::T;
     const int kv = k / VW;
     int gw = 1;
@@ -300,18 +236,10 @@ __device__ __forceinline__ void bupdate_rows(BSys &S, int k, double *rz_out, dou
     if (!any) return;
     const int64_t r0 = (int64_t)(blockIdx.x - S.unit0) * S.rows_per_unit;
     const int64_t r1 = min(S.A.n, r0 + S.rows_per_unit);
-    struct Flush {  // hand the partial sums out on every return path
-        TX *a, *b;
-        double *oa, *ob;
-        __device__ ~Flush() {
-#pragma unroll
-            for (int u = 0; u < VW; ++u) { oa[u] = (double)a[u]; ob[u] = (double)b[u]; }
-        }
-    } flush{rz, rr, rz_out, rr_out};
     V *X = reinterpret_cast<V *>(S.X), *R = reinterpret_cast<V *>(S.R);
     const V *P = reinterpret_cast<const V *>(S.P), *Q = reinterpret_cast<const V *>(S.Q);
     const bool f64 = sizeof(TX) == 8;
-    constexpr int RU4 = 2;  // rows in flight per thread
+    constexpr int RU4 = sizeof(V) >= 8 ? 2 : 4;  // rows in flight per thread
     for (int64_t rb = r0 + grp; rb < r1; rb += (int64_t)RU4 * ngrp) {
         V xv[RU4], rv[RU4], pv[RU4], qv[RU4];
         TX dd[RU4];
@@ -345,26 +273,16 @@ __device__ __forceinline__ void bupdate_rows(BSys &S, int k, double *rz_out, dou
     }
 }
 
-// per-column block sums of lane partials (VW per lane) in a fixed order
-__device__ __forceinline__ double col_lane_sum(const double *vals, int VW, int k, double *csum) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int kv = k / VW;
-    int gw = 1;
-    while (gw < kv) gw <<= 1;
-    const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
-    __syncthreads();
-    for (int i = threadIdx.x; i < NT / 32 * KMAX; i += NT) csum[i] = 0.0;
-    __syncthreads();
-    for (int g = 0; g < gpw; ++g) {
-        if (grp == g && jv < kv)
-            for (int u = 0; u < VW; ++u) csum[warp * KMAX + jv * VW + u] += vals[u];
-        __syncwarp();
-    }
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < (unsigned)k)
-        for (int w = 0; w < NT / 32; ++w) t += csum[w * KMAX + threadIdx.x];
-    return t;
+template <class TX, int VW>
+__device__ __forceinline__ void bupdate_block(BSys &S, int k, double *partials, double *csum) {
+    TX rz[VW], rr[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) { rz[u] = TX(0); rr[u] = TX(0); }
+    bupdate_rows<TX, VW>(S, k, rz, rr);
+    const double a = col_tree_sum<TX, VW>(rz, k, csum);
+    if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = a;
+    const double b = col_tree_sum<TX, VW>(rr, k, csum);
+    if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2 + 1) * KMAX + threadIdx.x] = b;
 }
 
 template <class TX>
@@ -377,14 +295,9 @@ __global__ void __launch_bounds__(NT, 4) k_bupdate(BSys *sys, const int *unit_sy
     if (S.active == 0) return;
     const int k = S.k, kw = S.kw;
     const int VW = vec_width<TX>(k);
-    double rz[4] = {0, 0, 0, 0}, rr[4] = {0, 0, 0, 0};
-    if (VW == 4) bupdate_rows<TX, (sizeof(TX) == 4 ? 4 : 2)>(S, k, rz, rr);
-    else if (VW == 2) bupdate_rows<TX, 2>(S, k, rz, rr);
-    else bupdate_rows<TX, 1>(S, k, rz, rr);
-    const double a = col_lane_sum(rz, VW, k, csum);
-    if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2) * KMAX + threadIdx.x] = a;
-    const double b = col_lane_sum(rr, VW, k, csum);
-    if (threadIdx.x < (unsigned)k) partials[((size_t)blockIdx.x * 2 + 1) * KMAX + threadIdx.x] = b;
+    if (VW == 4) bupdate_block<TX, (sizeof(TX) == 4 ? 4 : 2)>(S, k, partials, csum);
+    else if (VW == 2) bupdate_block<TX, 2>(S, k, partials, csum);
+    else bupdate_block<TX, 1>(S, k, partials, csum);
     if (sys_arrive_last(&S.ticket, S.nunits)) {
         const double rz_t = col_unit_sum_block(partials, S.unit0, S.nunits, 0, 2, kw, sm);
         const double rr_t = col_unit_sum_block(partials, S.unit0, S.nunits, 1, 2, kw, sm);
@@ -741,6 +654,8 @@ struct Batch {
     double *partials = nullptr;
     std::vector<void *> owned;
     int units = 0;
+    bool tma = false;  // every system has 32-row chunks: the TMA-streamed SpMM applies
+    ClassRanges cls;   // the unit table ordered by width class
     template <class T> int take(T **p, size_t n) {
         int rc = mem.alloc_n(p, n);
         if (rc == GB_OK) owned.push_back((void *)*p);
@@ -757,9 +672,51 @@ static int kw_of(int k) {
     return w;
 }
 
+// Units of a system (one block of the batched kernels each): consecutive
+// whole chunks of 32 rows, about 32 chunks per unit, at most 2048 units.  The
+// split depends on the system's own size only.
+static inline int units_of_rows(int64_t n, int64_t *rows_per_unit) {
+    const int64_t chunks = (n + 31) / 32;
+    const int64_t units = std::max<int64_t>(1, std::min<int64_t>((chunks + 31) / 32, 2048));
+    const int64_t cpu = (chunks + units - 1) / units;
+    *rows_per_unit = cpu * 32;
+    return (int)((chunks + cpu - 1) / cpu);
+}
+
+// Widest width class (0: k = 1 .. 5: k <= 32) that takes the TMA-streamed SpMM;
+// wider classes take the general kernel, whose lane groups gather a P row as
+// one coalesced segment.  Measured on 2D P2 1024^2 (SpMM ms, TMA / general):
+// fp32 k=1 0.16/0.27, k=8 0.32/0.43, k=16 0.49/0.71, k=32 1.17/1.09;
+// fp64 k=1 0.21/0.30, k=8 0.86/0.94, k=16 1.83/1.80, k=32 4.00/3.52.
+#ifndef GB_BSPMM_TMA_MAXC32
+#define GB_BSPMM_TMA_MAXC32 4
+#endif
+#ifndef GB_BSPMM_TMA_MAXC64
+#define GB_BSPMM_TMA_MAXC64 2
+#endif
+
+// SpMM of one iteration: one launch per width class present, over that
+// class's units, of the kernel the class takes (the TMA-streamed one needs
+// 32-row chunks in every system of the batch).
+template <class TX, class TV>
+static void launch_bspmm(bool tma, const ClassRanges &cr, int units, BSys *d_sys, const int *d_unit_sys,
+                         BGlobal *d_G, double *partials, cudaStream_t s) {
+    (void)units;
+    constexpr int maxc = sizeof(TX) == 8 ? GB_BSPMM_TMA_MAXC64 : GB_BSPMM_TMA_MAXC32;
+    for (int c = 0; c < ClassRanges::N; ++c) {
+        if (cr.count[c] <= 0) continue;
+        if (tma && c <= maxc) {
+            launch_bspmm_tma<TX, TV>(1 << c, cr.base[c], cr.count[c], d_sys, d_unit_sys, d_G, partials, s);
+        } else {
+            ::gb::count_launches(1);
+            k_bspmm<TX, TV><<<cr.count[c], NT, 0, s>>>(d_sys, d_unit_sys, cr.base[c], d_G, partials);
+        }
+    }
+}
+
 template <class TX, class TV>
 static void enqueue_biter(Batch &b, cudaStream_t s) {
-    ::gb::count_launches(1); k_bspmm<TX, TV><<<b.units, NT, 0, s>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
+    launch_bspmm<TX, TV>(b.tma, b.cls, b.units, b.d_sys, b.d_unit_sys, b.d_G, b.partials, s);
     ::gb::count_launches(1); k_bupdate<TX><<<b.units, NT, 0, s>>>(b.d_sys, b.d_unit_sys, b.d_G, b.partials);
     ::gb::count_launches(1); k_bpupdate<TX><<<b.units, NT, 0, s>>>(b.d_sys, b.d_unit_sys, b.d_G);
 }

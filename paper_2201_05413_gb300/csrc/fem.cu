@@ -468,6 +468,16 @@ static int assemble_impl(gb_fem_system *s, cudaStream_t st) {
     const int64_t n = s->n_free;
     int32_t *len = nullptr, *len_ib = nullptr;
     int *d_max = nullptr;
+    struct Temps {  // the row-length temporaries go back on every return path
+        Mem &m;
+        int32_t *&a, *&b;
+        int *&c;
+        ~Temps() {
+            m.release(a);
+            m.release(b);
+            m.release(c);
+        }
+    } temps{mem, len, len_ib, d_max};
     GB_TRY(mem.alloc_n(&len, (size_t)n + 1));
     GB_TRY(mem.alloc_n(&len_ib, (size_t)n + 1));
     GB_TRY(mem.alloc_n(&d_max, 1));
@@ -499,9 +509,6 @@ static int assemble_impl(gb_fem_system *s, cudaStream_t st) {
                                                  s->val_ib, s->diag);
     GB_CHECK_CUDA(cudaGetLastError());
     GB_CHECK_CUDA(cudaStreamSynchronize(st));
-    mem.release(len);
-    mem.release(len_ib);
-    mem.release(d_max);
     return GB_OK;
 }
 

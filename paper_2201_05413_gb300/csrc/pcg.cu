@@ -206,32 +206,6 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
     }
 }
 
-// 16-byte accesses of the streaming vector kernels: VW elements of T per load
-// (4 fp32 / 2 fp64); a type narrower than the step's element count (fp32
-// D^-1 beside fp64 vectors) takes fewer bytes per access.
-template <class T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
-template <class T, int N>
-__device__ __forceinline__ void ld_pack(const T *p, int64_t i, T (&o)[N]) {
-    if constexpr (sizeof(T) * N <= 16) {
-        const Pack<T, N> v = reinterpret_cast<const Pack<T, N> *>(p)[i];
-#pragma unroll
-        for (int k = 0; k < N; ++k) o[k] = v.v[k];
-    } else {
-        constexpr int H = N / 2;
-        const Pack<T, H> a = reinterpret_cast<const Pack<T, H> *>(p)[2 * i];
-        const Pack<T, H> b = reinterpret_cast<const Pack<T, H> *>(p)[2 * i + 1];
-#pragma unroll
-        for (int k = 0; k < H; ++k) { o[k] = a.v[k]; o[H + k] = b.v[k]; }
-    }
-}
-template <class T, int N>
-__device__ __forceinline__ void st_pack(T *p, int64_t i, const T (&o)[N]) {
-    Pack<T, N> v;
-#pragma unroll
-    for (int k = 0; k < N; ++k) v.v[k] = o[k];
-    reinterpret_cast<Pack<T, N> *>(p)[i] = v;
-}
-
 // Grid-stride over 16-byte groups, UPD_U groups per thread per step with every
 // load issued before the arithmetic (memory-level parallelism for these
 // streaming kernels); the n % VW last elements go to block 0.
@@ -1087,6 +1061,49 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
     }
     for (int k = 0; k < 3; ++k) h_ms[k] = tot[k] / iters;
     return rc;
+}
+
+// A bounded wait that must run out: one warp arms an mbarrier that nothing
+// will complete and waits on phase 0 with the library's bounded wait.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int *status, unsigned long long *waited_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const unsigned long long t0 = globaltimer();
+    const bool ok = mbar_wait(&bar, 0u, limit_ns);
+    const bool all = __all_sync(0xffffffffu, ok);
+    if (threadIdx.x == 0) {
+        *status = all ? ST_CONV : ST_TIMEOUT;
+        *waited_ns = globaltimer() - t0;
+    }
+}
+
+extern "C" int gbpcg_wait_selftest(double limit_ms, void *stream, double *h_waited_ms) {
+    GB_REQUIRE(limit_ms > 0.0 && limit_ms <= 2000.0, "gbpcg_wait_selftest: limit_ms must be in (0, 2000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *buf = nullptr;
+    GB_CHECK_CUDA(cudaMalloc(&buf, 16));
+    int *d_status = (int *)buf;
+    unsigned long long *d_waited = (unsigned long long *)((char *)buf + 8);
+    ::gb::count_launches(1);
+    k_wait_selftest<<<1, 32, 0, st>>>((unsigned long long)(limit_ms * 1e6), d_status, d_waited);
+    int h_status = -1;
+    unsigned long long h_waited = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_waited, d_waited, sizeof(h_waited), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) { set_error("gbpcg_wait_selftest: %s", cudaGetErrorString(e)); return GB_ECUDA; }
+    if (h_waited_ms) *h_waited_ms = (double)h_waited * 1e-6;
+    if (h_status == ST_TIMEOUT) {
+        set_error("gbpcg_wait_selftest: the bounded wait gave up after %.3f ms", (double)h_waited * 1e-6);
+        return GB_TIMEOUT;
+    }
+    return GB_OK;
 }
 
 extern "C" int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters,

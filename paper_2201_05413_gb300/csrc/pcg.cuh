@@ -58,6 +58,32 @@ __device__ __forceinline__ double sum_partials(const double *partials, int G, in
     return block_sum<NT>(s, smem);
 }
 
+// 16-byte accesses of the streaming vector kernels: VW elements of T per load
+// (4 fp32 / 2 fp64); a type narrower than the step's element count (fp32
+// D^-1 beside fp64 vectors) takes fewer bytes per access.
+template <class T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
+template <class T, int N>
+__device__ __forceinline__ void ld_pack(const T *p, int64_t i, T (&o)[N]) {
+    if constexpr (sizeof(T) * N <= 16) {
+        const Pack<T, N> v = reinterpret_cast<const Pack<T, N> *>(p)[i];
+#pragma unroll
+        for (int k = 0; k < N; ++k) o[k] = v.v[k];
+    } else {
+        constexpr int H = N / 2;
+        const Pack<T, H> a = reinterpret_cast<const Pack<T, H> *>(p)[2 * i];
+        const Pack<T, H> b = reinterpret_cast<const Pack<T, H> *>(p)[2 * i + 1];
+#pragma unroll
+        for (int k = 0; k < H; ++k) { o[k] = a.v[k]; o[H + k] = b.v[k]; }
+    }
+}
+template <class T, int N>
+__device__ __forceinline__ void st_pack(T *p, int64_t i, const T (&o)[N]) {
+    Pack<T, N> v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v.v[k] = o[k];
+    reinterpret_cast<Pack<T, N> *>(p)[i] = v;
+}
+
 __device__ __forceinline__ void stop(PcgScal *S, int status) {
     S->status = status;
     S->done = 1;

@@ -145,14 +145,6 @@ static int srv_take(gb_server *s, Slot &sl, T **p, size_t n) {
     return GB_OK;
 }
 
-static int units_of(int64_t n, int kw, int64_t *rows_per_unit) {
-    const int64_t groups = NT / kw;
-    int64_t units = (n + groups * 4 - 1) / (groups * 4);
-    units = std::max<int64_t>(1, std::min<int64_t>(units, 2048));
-    *rows_per_unit = (n + units - 1) / units;
-    return (int)((n + *rows_per_unit - 1) / *rows_per_unit);
-}
-
 static BSys desc_of(const Slot &sl, int unit0) {
     BSys S{};
     S.A = sl.A->view();
@@ -295,7 +287,7 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
     ::gb::count_launches(1);
     k_gather_rows<<<stride_grid((int64_t)nk, 256, 8), 256, 0, st>>>(L.n, L.k, L.A->perm, bfull, L.B64);
     // single-slot table: initial residual (x0 = 0), norms, thresholds
-    L.units = units_of(L.n, L.kw, &L.rows_per_unit);
+    L.units = units_of_rows(L.n, &L.rows_per_unit);
     GB_TRY(grow(s, &s->d_partials1, &s->cap_part1, (size_t)L.units * 3 * KMAX, st));
     std::vector<int> umap(L.units, 0);
     GB_TRY(grow(s, &s->d_unit1, &s->cap_umap1, (size_t)L.units, st));
@@ -506,14 +498,23 @@ static void server_loop(gb_server *s) {
         // A. launch a chunk of CG iterations for the iterating slots (main stream)
         std::vector<Slot *> it_slots;
         for (auto &p : s->slots) if (p->state == SL_ITER) it_slots.push_back(p.get());
+        // the table in width-class order: each class's units are contiguous
+        std::stable_sort(it_slots.begin(), it_slots.end(),
+                         [](const Slot *a, const Slot *b) { return width_class(a->k) < width_class(b->k); });
         bool launched = false;
         if (!it_slots.empty()) {
             std::vector<BSys> tab;
             std::vector<int> umap;
+            ClassRanges cls;
+            for (int c = 0; c < ClassRanges::N; ++c) cls.base[c] = -1;
             for (size_t i = 0; i < it_slots.size(); ++i) {
+                const int c = width_class(it_slots[i]->k);
+                if (cls.base[c] < 0) cls.base[c] = (int)umap.size();
                 tab.push_back(desc_of(*it_slots[i], (int)umap.size()));
                 for (int u = 0; u < it_slots[i]->units; ++u) umap.push_back((int)i);
+                cls.count[c] = (int)umap.size() - cls.base[c];
             }
+            for (int c = 0; c < ClassRanges::N; ++c) if (cls.base[c] < 0) cls.base[c] = 0;
             int rc = grow(s, &s->d_unit_sys, &s->cap_umap, umap.size(), s->main_st);
             if (rc == GB_OK) rc = grow(s, &s->d_partials, &s->cap_part, umap.size() * 3 * KMAX, s->main_st);
             BGlobal g{};
@@ -526,13 +527,13 @@ static void server_loop(gb_server *s) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_G, &g, sizeof(g), cudaMemcpyHostToDevice, s->main_st);
             const int U = (int)umap.size();
             for (int i = 0; i < s->opt.iters_per_step && e == cudaSuccess && rc == GB_OK; ++i) {
-                ::gb::count_launches(3);
+                ::gb::count_launches(2);
                 if (ru) {
-                    k_bspmm<float, float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    launch_bspmm<float, float>(true, cls, U, s->d_sys, s->d_unit_sys, s->d_G, s->d_partials, s->main_st);
                     k_bupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
                     k_bpupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
                 } else {
-                    k_bspmm<double, double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
+                    launch_bspmm<double, double>(true, cls, U, s->d_sys, s->d_unit_sys, s->d_G, s->d_partials, s->main_st);
                     k_bupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
                     k_bpupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
                 }

@@ -69,14 +69,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 #endif
     return ok != 0;
 }
-// bounded wait; true when the phase completed
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait; true when the phase completed, false when limit_ns passed
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         for (int i = 0; i < 8; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
