@@ -221,7 +221,9 @@ typedef struct PcgOptions {
     int32_t max_outer;     /* refinement steps cap (IR only); 0 = 30 */
     double inner_tol;      /* inner relative residual (IR only); 0 = 1e-4 */
     int32_t check_every;   /* iterations per host convergence poll; 0 = auto */
-    int32_t use_graph;     /* 1 = replay captured CUDA graphs (default), 0 = direct launches */
+    int32_t use_graph;     /* 1 = replay captured CUDA graphs (default), 0 = direct launches;
+                              GBPCG_USE_GRAPH=0 in the environment forces 0 (for launch-level
+                              profilers, which do not list a graph loop's replayed kernels) */
     int32_t x0_zero;       /* 1 = ignore d_x on entry and start from 0 */
     int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
 } PcgOptions;

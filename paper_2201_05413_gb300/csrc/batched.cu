@@ -184,6 +184,7 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     if (o.max_outer <= 0) o.max_outer = 30;
     if (!(o.inner_tol > 0)) o.inner_tol = 1e-4;
     if (o.check_every <= 0) o.check_every = 16;
+    if (graphs_disabled()) o.use_graph = 0;
     GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve_batched: bad precision");
     for (int s = 0; s < nsys; ++s) {
         GB_REQUIRE(o.precision != GB_F32_IR || A[s]->val32, "pcg_solve_batched: system %d has no fp32 values", s);

@@ -692,7 +692,7 @@ static inline int units_of_rows(int64_t n, int64_t *rows_per_unit) {
 #define GB_BSPMM_TMA_MAXC32 4
 #endif
 #ifndef GB_BSPMM_TMA_MAXC64
-#define GB_BSPMM_TMA_MAXC64 2
+#define GB_BSPMM_TMA_MAXC64 3
 #endif
 
 // SpMM of one iteration: one launch per width class present, over that

@@ -86,6 +86,11 @@ struct Mem {
 template <class In, class Out>
 int scan_exclusive(const In *in, Out *out, int64_t n, int64_t *h_total, Mem &mem);
 
+// GBPCG_USE_GRAPH=0 in the environment: solver loops run as direct launches
+// instead of CUDA-graph while-nodes (same kernels; for launch-level profilers,
+// which do not list the kernels a graph's device-side loop replays).
+bool graphs_disabled();
+
 // ------------------------------------------------------- launch geometry --
 int num_sms();
 // blocks per SM of the TMA-staged SpMV (fixed: its warp partition is built for it)

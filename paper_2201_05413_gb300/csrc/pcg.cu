@@ -5,10 +5,10 @@
 // One iteration = three kernels (Hestenes-Stiefel order, as in the oracle):
 //   k_spmv_pq  q = A p and the partial sums of p.q; the last block to finish
 //              reduces the partials in a fixed order and sets alpha = rho/p.q
-//   k_update   x += alpha p, r -= alpha q, z = D^-1 r (never stored), partial
-//              sums of r.z and r.r; the last block sets beta, rho, tests
-//              ||r||^2 <= tol^2 ||b||^2 (Eq. 2) and the iteration cap
-//   k_pupdate  p = D^-1 r + beta p
+//   k_update   x += alpha p, r -= alpha q, z = D^-1 r (stored in fp64 solves),
+//              partial sums of r.z and r.r; the last block sets beta, rho,
+//              tests ||r||^2 <= tol^2 ||b||^2 (Eq. 2) and the iteration cap
+//   k_pupdate  p = z + beta p (and the Eq. 2 test when the update deferred it)
 // The scalars live on the device, so the host never waits inside the loop:
 // the loop is a CUDA-graph while-node whose condition the finishing block
 // clears, or (use_graph=0) direct launches polled every few iterations.  Every
@@ -214,15 +214,28 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
 #endif
 constexpr int UPD_U = GB_UPD_U;
 
+// ||r||^2 is needed only when it can meet the Eq. (2) threshold: since
+// r.D^-1 r <= max(D^-1) ||r||^2, while rho = r.z stays above max(D^-1) times
+// the threshold (S->dmax > 0: max(D^-1) of the matrix) the x/r update skips
+// the r.r sums; when this iteration's r.z falls below that bound with r.r
+// skipped, the p update computes r.r from the r it reads anyway and makes the
+// test there, in the same iteration -- the stopping iteration is unchanged.
+__device__ __forceinline__ bool want_rr(const PcgScal *S) {
+    return !(S->dmax > 0.0) || S->rho <= S->dmax * S->thresh;
+}
+
+// x += alpha p, r -= alpha q, r.D^-1 r (and r.r, see want_rr); z = D^-1 r is
+// stored when z is given (the p update then reads it instead of D^-1 and r).
 template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX *__restrict__ r,
                                                const TX *__restrict__ p, const TX *__restrict__ q,
-                                               const TD *__restrict__ dinv, double *partials,
-                                               PcgScal *S) {
+                                               const TD *__restrict__ dinv, TX *__restrict__ z,
+                                               double *partials, PcgScal *S) {
     if (S->done) return;
     __shared__ double sm[NT / 32];
     constexpr int VW = 16 / sizeof(TX);
     const TX alpha = (TX)S->alpha;
+    const bool with_rr = want_rr(S);
     TX rz = TX(0), rr = TX(0);
     const int64_t ng = n / VW;
     const int64_t stride = (int64_t)gridDim.x * NT;
@@ -244,15 +257,18 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < ng) {
+                TX zv[VW];
 #pragma unroll
                 for (int k = 0; k < VW; ++k) {
                     xv[u][k] += alpha * pv[u][k];
                     rv[u][k] -= alpha * qv[u][k];
-                    rz += rv[u][k] * ((TX)dv[u][k] * rv[u][k]);
-                    rr += rv[u][k] * rv[u][k];
+                    zv[k] = (TX)dv[u][k] * rv[u][k];
+                    rz += rv[u][k] * zv[k];
+                    if (with_rr) rr += rv[u][k] * rv[u][k];
                 }
                 st_pack(x, i, xv[u]);
                 st_pack(r, i, rv[u]);
+                if (z) st_pack(z, i, zv);
             }
         }
     }
@@ -260,28 +276,32 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
         const int64_t i = ng * VW + threadIdx.x;
         const TX xi = x[i] + alpha * p[i];
         const TX ri = r[i] - alpha * q[i];
+        const TX zi = (TX)dinv[i] * ri;
         x[i] = xi;
         r[i] = ri;
-        rz += ri * ((TX)dinv[i] * ri);
-        rr += ri * ri;
+        if (z) z[i] = zi;
+        rz += ri * zi;
+        if (with_rr) rr += ri * ri;
     }
     const double a = block_sum<NT>((double)rz, sm);
-    const double b = block_sum<NT>((double)rr, sm);
+    const double b = with_rr ? block_sum<NT>((double)rr, sm) : 0.0;
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = a;
         partials[2 * blockIdx.x + 1] = b;
     }
     if (arrive_last(&S->ticket)) {
         const double rz_t = sum_partials(partials, gridDim.x, 2, 0, sm);
-        const double rr_t = sum_partials(partials, gridDim.x, 2, 1, sm);
+        const double rr_t = with_rr ? sum_partials(partials, gridDim.x, 2, 1, sm) : 0.0;
         if (threadIdx.x == 0) {
             S->ticket = 0;
             S->it += 1;
-            S->rr = rr_t;
-            if (!isfinite(rz_t) || !isfinite(rr_t)) stop(S, ST_BREAK);
-            else if (rr_t <= S->thresh) stop(S, ST_CONV);
+            if (with_rr) S->rr = rr_t;
+            if (!isfinite(rz_t) || (with_rr && !isfinite(rr_t))) stop(S, ST_BREAK);
+            else if (with_rr && rr_t <= S->thresh) stop(S, ST_CONV);
             else if (S->it >= S->maxit) stop(S, ST_MAXIT);
             else {
+                // r.r skipped but the test could pass now: the p update makes it
+                S->check_p = (!with_rr && rz_t <= S->dmax * S->thresh) ? 1 : 0;
                 S->beta = rz_t / S->rho;
                 S->rho = rz_t;
             }
@@ -289,24 +309,36 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, TX *__restrict__ x, TX
     }
 }
 
+// p = z + beta p with z = D^-1 r (read from z when given); when the x/r
+// update left the Eq. (2) test to this kernel (S->check_p), also r.r and the
+// test: a converged recurrence stops here, in the iteration that converged.
 template <class TX, class TD>
 __global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, const TX *__restrict__ r,
-                                                const TD *__restrict__ dinv, const PcgScal *S) {
+                                                const TD *__restrict__ dinv, const TX *__restrict__ z,
+                                                double *partials, PcgScal *S) {
     if (S->done) return;
+    __shared__ double sm[NT / 32];
     constexpr int VW = 16 / sizeof(TX);
     const TX beta = (TX)S->beta;
+    const bool check = S->check_p != 0;
+    TX rr = TX(0);
     const int64_t ng = n / VW;
     const int64_t stride = (int64_t)gridDim.x * NT;
     for (int64_t i0 = blockIdx.x * (int64_t)NT + threadIdx.x; i0 < ng; i0 += stride * UPD_U) {
-        TX pv[UPD_U][VW], rv[UPD_U][VW];
+        TX pv[UPD_U][VW], rv[UPD_U][VW], zv[UPD_U][VW];
         TD dv[UPD_U][VW];
 #pragma unroll
         for (int u = 0; u < UPD_U; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < ng) {
                 ld_pack(p, i, pv[u]);
-                ld_pack(r, i, rv[u]);
-                ld_pack(dinv, i, dv[u]);
+                if (z) {
+                    ld_pack(z, i, zv[u]);
+                    if (check) ld_pack(r, i, rv[u]);
+                } else {
+                    ld_pack(r, i, rv[u]);
+                    ld_pack(dinv, i, dv[u]);
+                }
             }
         }
 #pragma unroll
@@ -314,14 +346,33 @@ __global__ void __launch_bounds__(NT) k_pupdate(int64_t n, TX *__restrict__ p, c
             const int64_t i = i0 + u * stride;
             if (i < ng) {
 #pragma unroll
-                for (int k = 0; k < VW; ++k) pv[u][k] = (TX)dv[u][k] * rv[u][k] + beta * pv[u][k];
+                for (int k = 0; k < VW; ++k) {
+                    const TX zk = z ? zv[u][k] : (TX)dv[u][k] * rv[u][k];
+                    pv[u][k] = zk + beta * pv[u][k];
+                    if (check) rr += rv[u][k] * rv[u][k];
+                }
                 st_pack(p, i, pv[u]);
             }
         }
     }
     if (blockIdx.x == 0 && threadIdx.x < n - ng * VW) {
         const int64_t i = ng * VW + threadIdx.x;
-        p[i] = (TX)dinv[i] * r[i] + beta * p[i];
+        const TX zi = z ? z[i] : (TX)dinv[i] * r[i];
+        p[i] = zi + beta * p[i];
+        if (check) rr += r[i] * r[i];
+    }
+    if (!check) return;
+    const double b = block_sum<NT>((double)rr, sm);
+    if (threadIdx.x == 0) partials[2 * blockIdx.x + 1] = b;
+    if (arrive_last(&S->ticket)) {
+        const double rr_t = sum_partials(partials, gridDim.x, 2, 1, sm);
+        if (threadIdx.x == 0) {
+            S->ticket = 0;
+            S->rr = rr_t;
+            S->check_p = 0;
+            if (!isfinite(rr_t)) stop(S, ST_BREAK);
+            else if (rr_t <= S->thresh) stop(S, ST_CONV);
+        }
     }
 }
 
@@ -394,6 +445,7 @@ __global__ void __launch_bounds__(NT) k_start(int64_t n, const TX *__restrict__ 
             S->rho = t;
             S->done = 0;
             S->status = ST_RUN;
+            S->check_p = 0;
             if (!(t > 0.0)) { S->done = 1; S->status = t == 0.0 ? ST_CONV : ST_BREAK; }
         }
     }
@@ -493,7 +545,7 @@ static Grids pick_grids(int64_t n, int C) {
 
 template <class TV, class TX, class TD>
 static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
-                              TX *q, double *partials, PcgScal *S, const Grids &g, cudaStream_t st,
+                              TX *q, TX *z, double *partials, PcgScal *S, const Grids &g, cudaStream_t st,
                               int variant = 0) {
     if (variant == 0 && A.C == 32 && A.warp_chunk) launch_spmv_tma<TV, TX>(A, val, p, q, partials, S, st);
     else switch (A.C) {
@@ -501,8 +553,8 @@ static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, 
     case 64: ::gb::count_launches(1); k_spmv_pq<TV, TX, 64><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     default: ::gb::count_launches(1); k_spmv_pq<TV, TX, 128><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     }
-    ::gb::count_launches(1); k_update<TX, TD><<<g.upd, NT, 0, st>>>(A.n, x, r, p, q, dinv, partials, S);
-    ::gb::count_launches(1); k_pupdate<TX, TD><<<g.upd, NT, 0, st>>>(A.n, p, r, dinv, S);
+    ::gb::count_launches(1); k_update<TX, TD><<<g.upd, NT, 0, st>>>(A.n, x, r, p, q, dinv, z, partials, S);
+    ::gb::count_launches(1); k_pupdate<TX, TD><<<g.upd, NT, 0, st>>>(A.n, p, r, dinv, z, partials, S);
 }
 
 static void enqueue_residual(const SellView &A, const double *x, const double *b, double *r,
@@ -598,6 +650,7 @@ static PcgOptions defaults(const PcgOptions *o, int64_t n) {
     if (d.max_outer <= 0) d.max_outer = 30;
     if (!(d.inner_tol > 0)) d.inner_tol = 1e-4;
     if (d.check_every <= 0) d.check_every = (int)std::min<int64_t>(256, std::max<int64_t>(8, (1 << 20) / std::max<int64_t>(n, 1)));
+    if (graphs_disabled()) d.use_graph = 0;
     return d;
 }
 
@@ -629,10 +682,11 @@ static int map_status(int st) {
 struct Work {
     Mem mem;
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partials = nullptr;
+    double *z = nullptr;  // fp64 D^-1 r, when the workspace has room for it
     float *r32 = nullptr, *d32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     PcgScal *S = nullptr, *S2 = nullptr;
     ~Work() {
-        mem.release(x); mem.release(r); mem.release(p); mem.release(q); mem.release(b);
+        mem.release(x); mem.release(r); mem.release(p); mem.release(q); mem.release(b); mem.release(z);
         mem.release(partials);
         mem.release(r32); mem.release(d32); mem.release(p32); mem.release(q32);
         mem.release(S); mem.release(S2);
@@ -664,12 +718,14 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
     int64_t restarts = 0;
     int status = ST_RUN;
     double rel = std::sqrt(h.rr / h.bb);
+    // max(D^-1): the update defers its r.r sums while they cannot meet Eq. (2)
+    GB_CHECK_CUDA(cudaMemcpyAsync(&w.S->dmax, &A->dinv_max, sizeof(double), cudaMemcpyHostToDevice, st));
     while (rel > o.tol) {
         ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
         ++launches;
         GB_CHECK_CUDA(cudaGetLastError());
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.partials, w.S, g, s,
+            enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.z, w.partials, w.S, g, s,
                                                       o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr));
@@ -742,7 +798,7 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
         launches += 2;
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, (float *)nullptr, w.partials, w.S2, g, s,
                                                 o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
@@ -845,7 +901,7 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
         }
         const long long it0 = hr.it;
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.partials, w.S2, g, s,
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, (float *)nullptr, w.partials, w.S2, g, s,
                                                 o.spmv_variant ? o.spmv_variant : A->variant_hint);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
@@ -904,6 +960,7 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     GB_TRY(w.mem.alloc_n(&w.p, n));
     GB_TRY(w.mem.alloc_n(&w.q, n));
     GB_TRY(w.mem.alloc_n(&w.b, n));
+    GB_TRY(w.mem.alloc_n(&w.z, n));
     GB_TRY(w.mem.alloc_n(&w.partials, partial_slots(A, g)));
     GB_TRY(w.mem.alloc_n(&w.S, 1));
     GB_TRY(init_scal(w.S, o.max_iter, st));
@@ -975,6 +1032,7 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
     GB_TRY(w.mem.alloc_n(&w.p, n));
     GB_TRY(w.mem.alloc_n(&w.q, n));
     GB_TRY(w.mem.alloc_n(&w.b, n));
+    GB_TRY(w.mem.alloc_n(&w.z, n));
     GB_TRY(w.mem.alloc_n(&w.r32, n));
     GB_TRY(w.mem.alloc_n(&w.d32, n));
     GB_TRY(w.mem.alloc_n(&w.p32, n));
@@ -984,6 +1042,8 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
     PcgScal hs{};
     hs.maxit = (long long)iters + 1;
     hs.thresh = -1.0;  // never converges: every timed launch is a full pass
+    // fp64: the solver's launch sequence (z stored, r.r sums deferred)
+    if (precision == GB_F64) hs.dmax = A->dinv_max;
     GB_CHECK_CUDA(cudaMemcpyAsync(w.S, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
     GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
@@ -1013,9 +1073,9 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                     default: ::gb::count_launches(1); k_spmv_pq<double, double, 128><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<double, double><<<g.upd, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.partials, w.S);
+                    ::gb::count_launches(1); k_update<double, double><<<g.upd, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.z, w.partials, w.S);
                 } else {
-                    ::gb::count_launches(1); k_pupdate<double, double><<<g.upd, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.S);
+                    ::gb::count_launches(1); k_pupdate<double, double><<<g.upd, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.z, w.partials, w.S);
                 }
             } else {
                 if (k == 0) {
@@ -1033,9 +1093,9 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                         }
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<float, float><<<g.upd, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, w.partials, w.S);
+                    ::gb::count_launches(1); k_update<float, float><<<g.upd, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, (float *)nullptr, w.partials, w.S);
                 } else {
-                    ::gb::count_launches(1); k_pupdate<float, float><<<g.upd, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, w.S);
+                    ::gb::count_launches(1); k_pupdate<float, float><<<g.upd, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, (const float *)nullptr, w.partials, w.S);
                 }
             }
             cudaEventRecord(ev[3 * (size_t)i + k + 1], st);

@@ -19,11 +19,13 @@ struct PcgScal {
     double bb;      // ||b||^2
     double thresh;  // tol^2 ||b||^2
     double pz;      // reliable update: coefficient of z in the restored p
+    double dmax;    // max(D^-1) for the deferred r.r test (0: r.r every iteration)
     long long it, maxit;
     int done, status;
     unsigned int ticket;  // last-block counter
     int err;              // set by a kernel whose bounded wait ran out
     int use_cond;
+    int check_p;          // the p update makes this iteration's Eq. (2) test
     cudaGraphConditionalHandle cond;
 };
 enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3, ST_TIMEOUT = 4 };

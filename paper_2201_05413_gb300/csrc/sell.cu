@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include <cstring>
+
 #include "sell.cuh"
 
 namespace gb {
@@ -79,6 +81,15 @@ __global__ void k_perm_rows(int64_t n, const int32_t *perm, const int32_t *len, 
         dinv[r] = di;
         dinv32[r] = (float)di;
     }
+}
+
+// max of positive doubles through their bit patterns (order-preserving)
+__global__ void k_max_pos(int64_t n, const double *v, unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(v[i]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 __global__ void k_chunk_width(int64_t n, int64_t nchunks, int C, const int32_t *row_len,
@@ -221,6 +232,15 @@ static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const dou
     }
     STEPC(cudaGetLastError());
     ::gb::count_launches(1); k_perm_rows<<<grid, 256, 0, st>>>(n, A->perm, len, diag, A->iperm, A->row_len, A->dinv, A->dinv32);
+    {
+        unsigned long long *dmax = reinterpret_cast<unsigned long long *>(flags);  // 8 bytes: flags holds two ints
+        unsigned long long hmax = 0;
+        STEPC(cudaMemsetAsync(dmax, 0, sizeof(*dmax), st));
+        ::gb::count_launches(1); k_max_pos<<<grid, 256, 0, st>>>(n, A->dinv, dmax);
+        STEPC(cudaMemcpyAsync(&hmax, dmax, sizeof(hmax), cudaMemcpyDeviceToHost, st));
+        STEPC(cudaStreamSynchronize(st));
+        std::memcpy(&A->dinv_max, &hmax, sizeof(double));
+    }
     STEP(mem.alloc_n(&A->chunk_w, A->nchunks));
     STEP(mem.alloc_n(&A->chunk_ptr, A->nchunks + 1));
     STEP(mem.alloc_n(&chunk_sz, A->nchunks));

@@ -34,6 +34,7 @@ struct gb_sell {
     int16_t *col16 = nullptr;
     int nwarps = 0;
     int variant_hint = 0;  // SpMV variant solves use by default (set by sell_autotune)
+    double dinv_max = 0.0; // max_i 1/K_ii (host copy)
     int64_t *chunk_ptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
     float *val32 = nullptr, *dinv32 = nullptr;

@@ -25,6 +25,15 @@ void set_error(const char *fmt, ...) {
     g_last_error = buf;
 }
 
+bool graphs_disabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("GBPCG_USE_GRAPH");
+        v = (e && e[0] == '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
 int num_sms() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
