@@ -226,6 +226,9 @@ typedef struct PcgOptions {
                               profilers, which do not list a graph loop's replayed kernels) */
     int32_t x0_zero;       /* 1 = ignore d_x on entry and start from 0 */
     int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
+    int32_t persist_off;   /* pcg_solve_batched: 0 (default) = systems with n * k2 <= 32768 (k2: the
+                              power of two >= k) are solved whole by one CTA each in a single
+                              persistent launch; 1 = every system in the multi-launch loop */
 } PcgOptions;
 
 typedef struct PcgStats {

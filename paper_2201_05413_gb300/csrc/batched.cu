@@ -167,6 +167,28 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
     return GB_OK;
 }
 
+// One launch of the persistent kernel over the systems in `list` (their
+// initial residuals already formed): fp64 CG for fp64 batches, fp32 correction
+// solves in fp64 refinement otherwise.
+static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions &o, bool ir, cudaStream_t st) {
+    int *d_list = nullptr, *d_next = nullptr;
+    GB_TRY(b.take(&d_list, list.size()));
+    GB_TRY(b.take(&d_next, 1));
+    GB_CHECK_CUDA(cudaMemcpyAsync(d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), st));
+    PersistOpts po{};
+    po.tol = o.tol;
+    po.inner_tol = ir ? std::min(o.inner_tol, 1e-4) : 0.0;
+    po.maxit = o.max_iter;
+    po.max_outer = ir ? o.max_outer : 50;
+    const int grid = (int)std::min<size_t>(list.size(), (size_t)num_sms() * 2);
+    ::gb::count_launches(1);
+    if (ir) k_bpersist<float><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+    else k_bpersist<double><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+    GB_CHECK_CUDA(cudaGetLastError());
+    return GB_OK;
+}
+
 extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
                                  double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                                  PcgStats *stats) {
@@ -209,6 +231,24 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     std::vector<long long> inner_its(nsys, 0);
     std::vector<long long> restarts(nsys, 0);
     std::vector<long long> fallback_its(nsys, 0);
+    // small systems: solved whole by the persistent CTA-local kernel, one
+    // launch for all of them; the loops below then find them converged (or
+    // take over the columns it left above tol)
+    std::vector<int> plist;
+    for (int s = 0; s < nsys; ++s)
+        if (!o.persist_off && persist_eligible(A[s]->n, k[s])) plist.push_back(s);
+    if (!plist.empty()) {
+        GB_TRY(run_persist(b, plist, o, ir, st));
+        GB_TRY(pull_cols(b, hc, st));
+        std::vector<BSys> hs(nsys);
+        GB_CHECK_CUDA(cudaMemcpyAsync(hs.data(), b.d_sys, sizeof(BSys) * nsys, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));
+        for (int s : plist) {
+            long long mx = 0;
+            for (int j = 0; j < k[s]; ++j) mx = std::max(mx, hc.it[s][j]);
+            if (ir) { inner_its[s] = mx; outer_cnt[s] = hs[s].outer; }
+        }
+    }
     int rc = GB_OK;
     if (!ir) {
         // fp64 recurrences; restart columns whose true residual misses tol

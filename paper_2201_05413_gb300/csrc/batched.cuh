@@ -8,6 +8,7 @@
 
 #include "bsys.cuh"
 #include "bspmm_tma.cuh"
+#include "bpersist.cuh"
 
 namespace gb {
 

@@ -1,0 +1,328 @@
+// bpersist.cuh -- persistent, CTA-local Jacobi-PCG for the small systems of a
+// batch: one launch over a list of systems; each block takes the next system
+// from the list (atomic counter) and runs every iteration of all its columns
+// itself, with __syncthreads between the phases and block-level reductions,
+// until each column has met Eq. (2), hit the iteration cap or broken down.
+// No block waits on another, so there is nothing to spin on.
+//
+// A small system costs one block a few microseconds per iteration instead of
+// the three grid-wide launches of the batched loop, and many small systems
+// proceed side by side on different SMs.  A system's arithmetic depends only
+// on its own data (one block, fixed reduction order), so its result is the
+// same alone and in any batch.
+//
+// TX = double: fp64 CG on X64/R64 with D^-1 in fp64, restarted from the true
+// residual b - A x when the recursive one has met the threshold but the true
+// one has not (as the multi-kernel fp64 path).
+// TX = float: iterative refinement -- the fp64 residual r = b - A x, the test
+// and x += ||r|| d stay in fp64; the correction d solves A d = r / ||r|| by fp32
+// CG (fp32 values and vectors) to the relative residual inner_tol.
+//
+// Thread layout: kp = the power of two >= k; thread t owns column t mod kp (idle
+// when >= k) of rows t / kp, t / kp + PNT / kp, ...; per-column sums run an xor
+// tree over the lanes of a column and then the warps in order.
+#pragma once
+#include "bsys.cuh"
+
+namespace gb {
+
+constexpr int PNT = 512;                         // threads per block
+constexpr int64_t PERSIST_MAX_ELEMS = 1 << 15;   // n * kp of a system this kernel takes
+
+struct PersistOpts {
+    long long maxit;    // iterations per column (fp64) / inner iterations per outer step (fp32)
+    double tol;         // Eq. (2) threshold
+    double inner_tol;   // fp32 inner relative residual
+    int max_outer;      // refinement steps (fp32) / true-residual restarts (fp64)
+};
+
+// Per-column block sum; every thread passes its value, threads j < k read
+// out[j] after the call.  kp divides 32.
+__device__ __forceinline__ void p_colsum(double v, int kp, double (*red)[32], double *out) {
+    for (int o = kp; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < kp) red[warp][lane] = v;
+    __syncthreads();
+    if (threadIdx.x < (unsigned)kp) {
+        double s = 0.0;
+        for (int w = 0; w < PNT / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+struct PState {  // per-column scalars of the running recurrence (shared memory)
+    double alpha[32], beta[32], rho[32], thresh[32], rr[32], scale[32], t0[32], t1[32];
+    long long it[32];
+    int run[32];     // column iterating in the current recurrence
+    int status[32];  // ST_*
+};
+
+// q = A p for the columns of this thread, partial p.q; TV values, TX vectors.
+// The vectors are rewritten inside this kernel, so they are read with plain
+// (coherent) loads: no __restrict__ / read-only-cache loads on them.
+template <class TV, class TX>
+__device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict__ val, const TX *P, TX *Q,
+                                         int64_t n, int k, int kp, int j, bool on) {
+    double pq = 0.0;
+    if (!on) return pq;
+    const int C = A.C;
+    for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+        const int64_t c = r / C;
+        const int L = A.row_len[r];
+        const int64_t base = A.chunk_ptr[c] + (r - c * C);
+        TX acc = TX(0);
+        for (int s = 0; s < L; ++s) {
+            const int64_t e = base + (int64_t)s * C;
+            acc += (TX)ld_val(val + e) * P[(int64_t)__ldg(A.col + e) * k + j];
+        }
+        Q[r * k + j] = acc;
+        pq += (double)(P[r * k + j] * acc);
+    }
+    return pq;
+}
+
+// Runs CG on (X, R, P, Q) for the columns with st.run[j] set, stopping each at
+// ||R_j||^2 <= st.thresh[j], at st.it[j] == maxit, or on breakdown.  R holds the
+// starting residual; X is updated in place.
+template <class TV, class TX, class TD>
+__device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__restrict__ dinv, TX *X, TX *R, TX *P,
+                     TX *Q, int64_t n, int k, int kp, long long maxit, PState &st, double (*red)[32]) {
+    const int j = threadIdx.x % kp;
+    // start: P = D^-1 R, rho = R.D^-1 R
+    {
+        const bool on = j < k && st.run[j];
+        double rz = 0.0;
+        if (on)
+            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+                const TX z = (TX)dinv[r] * R[r * k + j];
+                P[r * k + j] = z;
+                rz += (double)(R[r * k + j] * z);
+            }
+        p_colsum(rz, kp, red, st.t0);
+        if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
+            const double t = st.t0[threadIdx.x];
+            st.rho[threadIdx.x] = t;
+            if (!(t > 0.0)) { st.run[threadIdx.x] = 0; st.status[threadIdx.x] = t == 0.0 ? ST_CONV : ST_BREAK; }
+        }
+        __syncthreads();
+    }
+    for (;;) {
+        int any = 0;
+        for (int q = 0; q < k; ++q) any |= st.run[q];
+        if (!any) break;
+        const bool on = j < k && st.run[j];
+        // q = A p, alpha = rho / p.q
+        const double pq = p_spmv<TV, TX>(A, val, P, Q, n, k, kp, j, on);
+        p_colsum(pq, kp, red, st.t0);
+        if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
+            const double t = st.t0[threadIdx.x];
+            if (!(t > 0.0) || !isfinite(t)) { st.run[threadIdx.x] = 0; st.status[threadIdx.x] = ST_BREAK; }
+            else st.alpha[threadIdx.x] = st.rho[threadIdx.x] / t;
+        }
+        __syncthreads();
+        // x += alpha p, r -= alpha q, r.D^-1 r, r.r
+        const bool on2 = j < k && st.run[j];
+        double rz = 0.0, rr = 0.0;
+        if (on2) {
+            const TX a = (TX)st.alpha[j];
+            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+                const int64_t e = r * k + j;
+                X[e] += a * P[e];
+                const TX rv = R[e] - a * Q[e];
+                R[e] = rv;
+                rz += (double)(rv * ((TX)dinv[r] * rv));
+                rr += (double)(rv * rv);
+            }
+        }
+        p_colsum(rz, kp, red, st.t0);
+        p_colsum(rr, kp, red, st.t1);
+        if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
+            const int q = threadIdx.x;
+            st.it[q] += 1;
+            st.rr[q] = st.t1[q];
+            if (!isfinite(st.t0[q]) || !isfinite(st.t1[q])) { st.run[q] = 0; st.status[q] = ST_BREAK; }
+            else if (st.t1[q] <= st.thresh[q]) { st.run[q] = 0; st.status[q] = ST_CONV; }
+            else if (st.it[q] >= maxit) { st.run[q] = 0; st.status[q] = ST_MAXIT; }
+            else { st.beta[q] = st.t0[q] / st.rho[q]; st.rho[q] = st.t0[q]; }
+        }
+        __syncthreads();
+        // p = D^-1 r + beta p
+        const bool on3 = j < k && st.run[j];
+        if (on3) {
+            const TX b = (TX)st.beta[j];
+            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+                const int64_t e = r * k + j;
+                P[e] = (TX)dinv[r] * R[e] + b * P[e];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// R64 = B64 - A X64 in fp64 for the columns in `sel`; ||R64_j||^2 into st.rr.
+static __device__ void p_resid(const BSys &S, int64_t n, int k, int kp, const int *sel, PState &st, double (*red)[32]) {
+    const int j = threadIdx.x % kp;
+    double rr = 0.0;
+    if (j < k && sel[j]) {
+        const SellView &A = S.A;
+        const int C = A.C;
+        for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+            const int64_t c = r / C;
+            const int L = A.row_len[r];
+            const int64_t base = A.chunk_ptr[c] + (r - c * C);
+            double acc = 0.0;
+            for (int s = 0; s < L; ++s) {
+                const int64_t e = base + (int64_t)s * C;
+                acc += ld_val(A.val + e) * S.X64[(int64_t)__ldg(A.col + e) * k + j];
+            }
+            const double ri = S.B64[r * k + j] - acc;
+            S.R64[r * k + j] = ri;
+            rr += ri * ri;
+        }
+    }
+    p_colsum(rr, kp, red, st.t1);
+    if (threadIdx.x < (unsigned)k && sel[threadIdx.x]) st.rr[threadIdx.x] = st.t1[threadIdx.x];
+    __syncthreads();
+}
+
+// One system, fp64 recurrences.  Entry state (from the batch's initial
+// residual kernel): R64 = B - A X0, c.rr, c.bb, c.thresh.
+static __device__ void p_solve_f64(BSys &S, const PersistOpts &o, PState &st, double (*red)[32], int *sel) {
+    const int64_t n = S.A.n;
+    const int k = S.k;
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    if (threadIdx.x < 32) {
+        const int q = threadIdx.x;
+        st.it[q] = 0;
+        st.run[q] = 0;
+        st.status[q] = ST_CONV;
+        if (q < k) {
+            st.thresh[q] = S.c.thresh[q];
+            st.rr[q] = S.c.rr[q];
+        }
+    }
+    __syncthreads();
+    for (int round = 0; round <= o.max_outer; ++round) {
+        // columns whose true residual is above the threshold and that may go on
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            const bool go = q < k && S.c.bb[q] > 0.0 && st.rr[q] > st.thresh[q] &&
+                            (round == 0 || st.status[q] == ST_CONV) && st.it[q] < o.maxit;
+            st.run[q] = go ? 1 : 0;
+            sel[q] = go ? 1 : 0;
+            if (go) st.status[q] = ST_RUN;
+        }
+        __syncthreads();
+        int any = 0;
+        for (int q = 0; q < k; ++q) any |= sel[q];
+        if (!any) break;
+        p_cg<double, double, double>(S.A, S.A.val, S.A.dinv, S.X64, S.R64, (double *)S.P, (double *)S.Q, n, k, kp,
+                                     o.maxit, st, red);
+        p_resid(S, n, k, kp, sel, st, red);  // true residual of the columns just run
+        if (round == o.max_outer && threadIdx.x < (unsigned)k && sel[threadIdx.x] &&
+            st.rr[threadIdx.x] > st.thresh[threadIdx.x] && st.status[threadIdx.x] == ST_CONV)
+            st.status[threadIdx.x] = ST_MAXIT;
+        __syncthreads();
+    }
+}
+
+// One system, fp32 correction solves inside fp64 refinement.
+static __device__ void p_solve_ir(BSys &S, const PersistOpts &o, PState &st, double (*red)[32], int *sel) {
+    const int64_t n = S.A.n;
+    const int k = S.k;
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    const int j = threadIdx.x % kp;
+    float *D = (float *)S.X, *R = (float *)S.R, *P = (float *)S.P, *Q = (float *)S.Q;
+    if (threadIdx.x < 32) {
+        const int q = threadIdx.x;
+        st.it[q] = 0;
+        st.status[q] = ST_CONV;
+        if (q < k) st.rr[q] = S.c.rr[q];
+    }
+    __syncthreads();
+    long long inner_total = 0;
+    int outer = 0;
+    for (; outer < o.max_outer; ++outer) {
+        // columns above the threshold: scale their residual down to unit norm
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            const bool go = q < k && S.c.bb[q] > 0.0 && st.rr[q] > S.c.thresh[q];
+            sel[q] = go ? 1 : 0;
+            st.run[q] = go ? 1 : 0;
+            st.scale[q] = go ? sqrt(st.rr[q]) : 1.0;
+            st.thresh[q] = o.inner_tol * o.inner_tol;  // ||R32||^2 relative to 1
+            if (go) st.status[q] = ST_RUN;
+        }
+        __syncthreads();
+        int any = 0;
+        for (int q = 0; q < k; ++q) any |= sel[q];
+        if (!any) break;
+        if (j < k && sel[j]) {
+            const double sc = 1.0 / st.scale[j];
+            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+                R[r * k + j] = (float)(sc * S.R64[r * k + j]);
+                D[r * k + j] = 0.0f;
+            }
+        }
+        if (threadIdx.x < 32) st.it[threadIdx.x] = 0;
+        __syncthreads();
+        p_cg<float, float, float>(S.A, S.A.val32, S.A.dinv32, D, R, P, Q, n, k, kp, o.maxit, st, red);
+        long long mx = 0;
+        for (int q = 0; q < k; ++q) if (sel[q]) mx = max(mx, st.it[q]);
+        inner_total += mx;
+        // x += ||r|| d in fp64, then the true residual
+        if (j < k && sel[j]) {
+            const double sc = st.scale[j];
+            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) S.X64[r * k + j] += sc * (double)D[r * k + j];
+        }
+        __syncthreads();
+        p_resid(S, n, k, kp, sel, st, red);
+    }
+    if (threadIdx.x < (unsigned)k) {
+        const int q = threadIdx.x;
+        st.status[q] = (S.c.bb[q] == 0.0 || st.rr[q] <= S.c.thresh[q]) ? ST_CONV : ST_MAXIT;
+        st.it[q] = inner_total;
+    }
+    if (threadIdx.x == 0) S.outer = outer;
+    __syncthreads();
+}
+
+template <class TX>
+__global__ void __launch_bounds__(PNT) k_bpersist(BSys *sys, const int *list, int nlist, int *next, PersistOpts o) {
+    __shared__ PState st;
+    __shared__ double red[PNT / 32][32];
+    __shared__ int sel[32];
+    __shared__ int idx;
+    for (;;) {
+        if (threadIdx.x == 0) idx = atomicAdd(next, 1);
+        __syncthreads();
+        const int i = idx;
+        __syncthreads();
+        if (i >= nlist) break;
+        BSys &S = sys[list[i]];
+        if (sizeof(TX) == 8) p_solve_f64(S, o, st, red, sel);
+        else p_solve_ir(S, o, st, red, sel);
+        // column state for the host, as the batched loop leaves it
+        if (threadIdx.x < (unsigned)S.k) {
+            const int q = threadIdx.x;
+            S.c.rr[q] = st.rr[q];
+            S.c.status[q] = st.status[q];
+            S.c.it[q] = st.it[q];
+            S.c.done[q] = 1;
+        }
+        if (threadIdx.x == 0) S.active = 0;
+        __syncthreads();
+    }
+}
+
+// Whether a system goes to the persistent kernel.
+inline bool persist_eligible(int64_t n, int k) {
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    return n * kp <= PERSIST_MAX_ELEMS;
+}
+
+}  // namespace gb

@@ -27,6 +27,7 @@ struct BSys {
     int64_t rows_per_unit;
     unsigned int ticket;
     int active;  // columns still iterating
+    int outer;   // refinement steps made by the persistent kernel
 };
 
 struct BGlobal {

@@ -318,6 +318,50 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
         mask[j] = ru ? 2 : 1;
         target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
     }
+    if (persist_eligible(L.n, L.k)) {
+        // small request: solved whole right here by one block of the persistent
+        // kernel; converged columns are final, any other goes on in the slot
+        // machinery from the current x
+        const int one[2] = {0, 0};  // list = {system 0 of the single-slot table}, counter
+        PersistOpts po{};
+        po.tol = s->opt.tol;
+        po.inner_tol = 1e-4;
+        po.maxit = std::min<long long>(s->opt.max_iter, 20 * (long long)L.n + 100);
+        po.max_outer = ru ? 30 : 50;
+        e = cudaMemcpyAsync(s->d_mask1, one, sizeof(one), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail("persist list", e);
+        ::gb::count_launches(1);
+        if (ru) k_bpersist<float><<<1, PNT, 0, st>>>(s->d_sys1, s->d_mask1, 1, s->d_mask1 + 1, po);
+        else k_bpersist<double><<<1, PNT, 0, st>>>(s->d_sys1, s->d_mask1, 1, s->d_mask1 + 1, po);
+        std::vector<int> stat(L.k);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rr.data(), L.c.rr, sizeof(double) * L.k, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stat.data(), L.c.status, sizeof(int) * L.k, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && ru) e = cudaMemsetAsync(L.X, 0, sizeof(float) * nk, st);  // its correction is in X64
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail("persistent solve", e);
+        std::vector<int> rearm(KMAX, 0);
+        std::vector<long long> it0(KMAX, 0);
+        bool left = false;
+        for (int j = 0; j < L.k; ++j) {
+            if (L.fin[j]) continue;
+            L.rel[j] = std::sqrt(rr[j] / bb[j]);
+            if (L.rel[j] <= s->opt.tol) { L.fin[j] = 1; L.fstat[j] = GB_OK; }
+            else { rearm[j] = ST_BREAK; left = true; }  // the service step re-arms it with a fresh direction
+        }
+        if (left) {
+            e = cudaMemcpyAsync(L.c.status, rearm.data(), sizeof(int) * L.k, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(L.c.it, it0.data(), sizeof(long long) * L.k, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return fail("persistent re-arm", e);
+        }
+        L.active = 0;
+        L.state = SL_SERVICE;  // the service step retires it (or re-arms what is left)
+        L.bytes = s->slot_bytes_acc;
+        L.t_admit = now_ms();
+        out = std::move(sl);
+        return GB_OK;
+    }
     e = cudaMemcpyAsync(s->d_mask1, mask.data(), sizeof(int) * KMAX, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L.c.target, target.data(), sizeof(double) * KMAX, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail("mask", e);

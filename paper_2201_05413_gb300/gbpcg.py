@@ -61,7 +61,8 @@ class gb_sell_info(C.Structure):
 class PcgOptions(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("check_every", C.c_int32),
-                ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("spmv_variant", C.c_int32)]
+                ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("spmv_variant", C.c_int32),
+                ("persist_off", C.c_int32)]
 
 
 class PcgStats(C.Structure):

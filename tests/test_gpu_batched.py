@@ -29,16 +29,17 @@ def _oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k):
     return s, rp, ci, v, B, X
 
 
+@pytest.mark.parametrize("persist_off", [0, 1])
 @pytest.mark.parametrize("k", [1, 3, 8, 32])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_multi_rhs_matches_oracle(P, k, prec):
+def test_multi_rhs_matches_oracle(P, k, prec, persist_off):
     spec = (2, 2, 24, 1, 1, 2)
     coef = np.random.default_rng(3).standard_normal((k, 10))
     d = P.FemSystem(*spec)
     A = d.to_sell(32, 256)
     B = d.lift(d.dirichlet(O.G_HARMONIC, coef, k))
     p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
-    Xs, stats = P.pcg_solve_batched([A], [B], tol=TOL, precision=p, max_iter=100000)
+    Xs, stats = P.pcg_solve_batched([A], [B], tol=TOL, precision=p, max_iter=100000, persist_off=persist_off)
     X = Xs[0].cpu().numpy()
     s, rp, ci, v, Bo, Xo = _oracle_cols(*spec, O.G_HARMONIC, coef, k)
     for j in range(k):
@@ -48,7 +49,8 @@ def test_multi_rhs_matches_oracle(P, k, prec):
     assert stats[0]["status"] == 0 and stats[0]["relres"] <= TOL
 
 
-def test_uneven_systems_one_batch(P):
+@pytest.mark.parametrize("persist_off", [0, 1])
+def test_uneven_systems_one_batch(P, persist_off):
     specs = [(2, 1, 20, 1, 1, 1, 1), (2, 2, 13, 1, 1, 2, 3), (3, 1, 9, 0, 0, 0, 2), (3, 2, 5, 0, 0, 0, 5)]
     mats, Bs, refs = [], [], []
     rng = np.random.default_rng(7)
@@ -59,7 +61,7 @@ def test_uneven_systems_one_batch(P):
         mats.append(d.to_sell(32, 64))
         Bs.append(d.lift(d.dirichlet(gid, coef, k)))
         refs.append(_oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k))
-    Xs, stats = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=100000)
+    Xs, stats = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=100000, persist_off=persist_off)
     for X, (s, rp, ci, v, Bo, Xo), st in zip(Xs, refs, stats):
         X = X.cpu().numpy()
         assert st["status"] == 0
@@ -67,7 +69,7 @@ def test_uneven_systems_one_batch(P):
             assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8
     # each result equals the same system solved alone, bit for bit
     for i in range(len(mats)):
-        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, max_iter=100000)
+        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, max_iter=100000, persist_off=persist_off)
         assert bool((Xa[0] == Xs[i]).all())
         assert sa[0]["iterations"] == stats[i]["iterations"]
 
@@ -102,3 +104,32 @@ def test_batched_zero_column_and_errors(P):
     assert torch.count_nonzero(Xs[0][:, 1]).item() == 0
     with pytest.raises(P.GbError):
         P.pcg_solve_batched([A], [torch.zeros((d.n_free, 33), dtype=torch.float64, device="cuda")])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_persistent_and_multilaunch_mix(P, prec):
+    """A batch with systems below and above the persistent kernel's size limit
+    (n * k2 <= 32768): every column meets Eq. 2 and matches the oracle, and the
+    persistent and multi-launch solves of the same batch agree to the solver
+    tolerance."""
+    specs = [(2, 1, 16, 1, 1, 3, 4), (2, 1, 200, 1, 1, 4, 1), (3, 1, 12, 0, 0, 0, 8), (2, 2, 40, 1, 1, 5, 2)]
+    mats, Bs, refs = [], [], []
+    rng = np.random.default_rng(21)
+    for dim, deg, cells, jit, dm, seed, k in specs:
+        d = P.FemSystem(dim, deg, cells, jit, dm, seed)
+        gid = O.G_HARMONIC if dim == 2 else O.G_LINEAR
+        coef = rng.standard_normal((k, O.NCOEF[gid]))
+        mats.append(d.to_sell(32, 256))
+        Bs.append(d.lift(d.dirichlet(gid, coef, k)))
+        refs.append(_oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k))
+    p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
+    Xp, sp = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=200000, persist_off=0)
+    Xm, sm = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=200000, persist_off=1)
+    for X1, X2, s1, s2, (s, rp, ci, v, Bo, Xo) in zip(Xp, Xm, sp, sm, refs):
+        assert s1["status"] == 0 and s2["status"] == 0
+        X1, X2 = X1.cpu().numpy(), X2.cpu().numpy()
+        for j in range(X1.shape[1]):
+            rel = np.linalg.norm(Bo[:, j] - O.spmv(rp, ci, v, X1[:, j])) / np.linalg.norm(Bo[:, j])
+            assert rel <= 1.5 * TOL, (j, rel)
+            assert O.x_err(Xo[:, j], X1[:, j]) <= 1e-8
+            assert O.x_err(X2[:, j], X1[:, j]) <= 1e-8
