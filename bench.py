@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
                     help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--sweep", default=None, choices=["eps", "rhs"],
+                    help="accuracy vs stopping tolerance (eps) or solve time vs number of right-hand sides (rhs)")
     ap.add_argument("--profile-iters", type=int, default=3)
     return ap.parse_args()
 
@@ -484,10 +486,93 @@ def run_serving(nreq, seed=4):
             "speedup_saturated_vs_one_at_a_time": round(seq / wall, 3)}
 
 
+EPS_SYSTEMS = [  # (name, spec, gid, closed form available)
+    ("2D-P1-jittered-1024", (2, 1, 1024, 1, 1, 1), 1, False),
+    ("2D-P2-jittered-1024", (2, 2, 1024, 1, 1, 1), 1, True),
+    ("3D-P1-Kuhn-128", (3, 1, 128, 0, 0, 0), 2, True),
+    ("3D-P2-Kuhn-64", (3, 2, 64, 0, 0, 0), 2, True),
+]
+
+
+def run_sweep_eps():
+    """Accuracy and time against the stopping tolerance of Eq. (2), fp64 and
+    fp32 recurrences with fp64 reliable updates; x_err (Eq. 1) against the
+    exact discrete solution where the discretisation reproduces g exactly
+    (P2 in 2D and 3D, the 7-point Kuhn P1 on quadratics), else against the
+    fp64 solve at 1e-13."""
+    import torch
+    import paper_2201_05413_gb300 as P
+    P.load()
+    for name, spec, gid, exact in EPS_SYSTEMS:
+        d = P.FemSystem(*spec)
+        A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32)
+        b = d.lift(d.dirichlet(gid))[:, 0]
+        if exact:
+            ref = d.dirichlet(gid, which="free")[:, 0]
+        else:
+            ref, _ = A.solve(b, tol=1e-13, max_iter=2000000, raise_on_fail=False)
+        for tol in (1e-6, 1e-8, 1e-10, 1e-12, 1e-14):
+            for pn, pv in (("f64", P.GB_F64), ("f32_ru", P.GB_F32_RU)):
+                x, st = A.solve(b, tol=tol, max_iter=2000000, precision=pv, raise_on_fail=False)
+                torch.cuda.synchronize()
+                err = float((x - ref).norm() / ref.norm())
+                print(json.dumps({"sweep": "eps", "system": name, "tol": tol, "precision": pn,
+                                  "status": st["status"], "iterations": st["iterations"], "relres": st["relres"],
+                                  "x_err": err, "x_err_reference": "exact discrete solution" if exact else
+                                  "fp64 solve at 1e-13", "solve_ms": round(st["solve_ms"], 2)}), flush=True)
+        del A, d
+        torch.cuda.empty_cache()
+
+
+def run_sweep_rhs():
+    """Time to solve k right-hand sides of one system (2D jittered P2 256^2,
+    harmonic-basis Dirichlet data), blocked (Eq. MRH: k recurrences sharing one
+    SpMM pass, in groups of up to 32 columns per system of the batch) against
+    one pcg_solve per column, fp64 and fp32 recurrences."""
+    import numpy as np
+    import torch
+    import paper_2201_05413_gb300 as P
+    P.load()
+    spec = (2, 2, 256, 1, 1, 5)
+    d = P.FemSystem(*spec)
+    A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32)
+    for k in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+        coef = np.random.default_rng(11).standard_normal((k, 10))
+        B = d.lift(d.dirichlet(4, coef, k))
+        groups = [B[:, j:j + 32].contiguous() for j in range(0, k, 32)]
+        row = {"sweep": "rhs", "system": "2D-P2-jittered-256", "n": A.n, "nnz": A.nnz, "k": k}
+        for pn, pv, pb in (("f64", P.GB_F64, P.GB_F64), ("f32", P.GB_F32_RU, P.GB_F32_IR)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, sts = P.pcg_solve_batched([A] * len(groups), groups, tol=TOL, max_iter=2000000, precision=pb,
+                                         raise_on_fail=False)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            if k <= 64:
+                for j in range(k):
+                    A.solve(B[:, j].contiguous(), tol=TOL, max_iter=2000000, precision=pv, raise_on_fail=False)
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+            else:
+                ts = None
+            row[pn] = {"blocked_s": round(tb, 4), "blocked_ms_per_rhs": round(1e3 * tb / k, 3),
+                       "one_at_a_time_s": None if ts is None else round(ts, 4),
+                       "one_at_a_time_ms_per_rhs": None if ts is None else round(1e3 * ts / k, 3),
+                       "max_relres": max(x["relres"] for x in sts), "status": max(abs(x["status"]) for x in sts)}
+        print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
     if args.profile_kernels:
         run_profile(args)
+        return
+    if args.sweep == "eps":
+        run_sweep_eps()
+        return
+    if args.sweep == "rhs":
+        run_sweep_rhs()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -278,7 +278,8 @@ typedef struct ServeOptions {
     int32_t precision;       /* GB_F32_RU or GB_F64 */
     double tol;              /* Eq. (2) threshold (0 = 1e-10) */
     int64_t max_iter;        /* iterations per column (0 = 10^6) */
-    int32_t iters_per_step;  /* CG iterations between scheduling points (0 = 200) */
+    int32_t iters_per_step;  /* CG iterations between scheduling points; 0 = adaptive (default):
+                                about 10 ms of the resident requests' iterations, 4 to 200 */
     int32_t device;          /* CUDA device, -1 = the current one */
 } ServeOptions;
 

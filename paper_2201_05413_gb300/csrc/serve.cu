@@ -7,7 +7,8 @@
 // runs, pending requests are admitted on the side stream as slots and memory
 // allow: device assembly, SELL conversion, Dirichlet lift and the start of
 // their recurrences, allocated from a stream-ordered pool and charged against
-// the memory budget.  A chunk ends after iters_per_step iterations or as soon
+// the memory budget.  A chunk ends after iters_per_step iterations (adaptive by
+// default: about 10 ms of the resident set's iterations) or as soon
 // as a slot's columns have all stopped; the thread then services those slots
 // (fp32 recurrences: the reliable update -- x += d and r = b - A x in fp64,
 // the fp64 test, residual replacement; fp64 recurrences: the true-residual
@@ -26,6 +27,8 @@
 #include "batched.cuh"
 
 namespace gb {
+
+constexpr double CHUNK_MS = 10.0;  // target length of a chunk in adaptive mode
 
 static bool log_on() {
     static int v = -1;
@@ -81,6 +84,8 @@ struct gb_server {
     int dev = 0;
     cudaStream_t main_st = nullptr, side_st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing of a chunk (adaptive chunk length)
+    int ips = 16;                            // iterations of the next chunk (adaptive mode)
     std::thread th;
     std::mutex mu;
     std::condition_variable cv;
@@ -565,12 +570,15 @@ static void server_loop(gb_server *s) {
             g.maxit = s->opt.max_iter;
             g.active_systems = (int)it_slots.size();
             g.stop_on_retire = 1;
-            g.budget = s->opt.iters_per_step;
+            const bool adaptive = s->opt.iters_per_step <= 0;
+            const int ips = adaptive ? s->ips : s->opt.iters_per_step;
+            g.budget = ips;
             cudaError_t e = cudaMemcpyAsync(s->d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, s->main_st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, s->main_st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_G, &g, sizeof(g), cudaMemcpyHostToDevice, s->main_st);
             const int U = (int)umap.size();
-            for (int i = 0; i < s->opt.iters_per_step && e == cudaSuccess && rc == GB_OK; ++i) {
+            if (e == cudaSuccess && adaptive) e = cudaEventRecord(s->ev0, s->main_st);
+            for (int i = 0; i < ips && e == cudaSuccess && rc == GB_OK; ++i) {
                 ::gb::count_launches(2);
                 if (ru) {
                     launch_bspmm<float, float>(true, cls, U, s->d_sys, s->d_unit_sys, s->d_G, s->d_partials, s->main_st);
@@ -583,6 +591,7 @@ static void server_loop(gb_server *s) {
                 }
             }
             if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess && adaptive) e = cudaEventRecord(s->ev1, s->main_st);
             if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->main_st);
             if (e != cudaSuccess || rc != GB_OK) {
                 s->fatal = e != cudaSuccess ? GB_ECUDA : rc;
@@ -621,6 +630,21 @@ static void server_loop(gb_server *s) {
         // C. wait for the chunk, pull the column states of the slots in it
         if (launched) {
             cudaError_t e = cudaEventSynchronize(s->ev);
+            if (e == cudaSuccess && s->opt.iters_per_step <= 0) {
+                // adaptive chunk length: about CHUNK_MS of iterations of the
+                // current resident set per chunk, so that arrivals are admitted
+                // (and small requests solved) within about that long
+                BGlobal hg{};
+                float ms = 0.f;
+                e = cudaMemcpy(&hg, s->d_G, sizeof(hg), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->ev0, s->ev1);
+                const int done_its = std::max(1, s->ips - std::max(0, hg.budget));
+                if (e == cudaSuccess && ms > 0.f) {
+                    const double per_it = (double)ms / done_its;
+                    const double want = CHUNK_MS / std::max(per_it, 1e-3);
+                    s->ips = (int)std::max(4.0, std::min(200.0, want));
+                }
+            }
             for (Slot *L : it_slots) {
                 if (e != cudaSuccess) break;
                 std::vector<int> done(L->k);
@@ -667,12 +691,14 @@ extern "C" int serve_create(const ServeOptions *opt, gb_server **out) {
     s->opt = *opt;
     if (!(s->opt.tol > 0)) s->opt.tol = 1e-10;
     if (s->opt.max_iter <= 0) s->opt.max_iter = 1000000;
-    if (s->opt.iters_per_step <= 0) s->opt.iters_per_step = 200;
+    if (s->opt.iters_per_step < 0) s->opt.iters_per_step = 0;
     if (opt->device >= 0) GB_CHECK_CUDA(cudaSetDevice(opt->device));
     GB_CHECK_CUDA(cudaGetDevice(&s->dev));
     GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->main_st, cudaStreamNonBlocking));
     GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking));
     GB_CHECK_CUDA(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+    GB_CHECK_CUDA(cudaEventCreate(&s->ev0));
+    GB_CHECK_CUDA(cudaEventCreate(&s->ev1));
     s->alloc.ctx = s;
     s->alloc.alloc = srv_alloc;
     s->alloc.free = srv_free;
@@ -742,6 +768,8 @@ extern "C" void serve_destroy(gb_server *s) {
     cudaFree(s->d_sys); cudaFree(s->d_unit_sys); cudaFree(s->d_mask); cudaFree(s->d_G); cudaFree(s->d_partials);
     cudaFree(s->d_sys1); cudaFree(s->d_unit1); cudaFree(s->d_mask1); cudaFree(s->d_partials1);
     cudaEventDestroy(s->ev);
+    cudaEventDestroy(s->ev0);
+    cudaEventDestroy(s->ev1);
     cudaStreamDestroy(s->main_st);
     cudaStreamDestroy(s->side_st);
     delete s;
