@@ -127,6 +127,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------- ranks (N > 1) --
+def reduce_timing(total_s, units_per_rank, world, device):
+    """Whole-job timing of N replicas: the slowest rank's time (max over
+    ranks) and units of all ranks per second.  Every rank calls it."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return total_s, units_per_rank * world / total_s
+
+
 # ------------------------------------------------------------- our arm --
 def run_ours(args, rank, world):
     import torch
@@ -192,14 +205,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clocks = clk.stop()
     barrier()
-    total = sum(t64)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
-    solves = len(SYSTEMS) * args.steps * world
-    value = solves / total
+    total, value = reduce_timing(sum(t64), len(SYSTEMS) * args.steps, world, "cuda")
 
     # ---- mixed precision (fp32 recurrence, fp64 reliable updates), same workload
     mixed_info = []
