@@ -72,7 +72,21 @@ __device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict
         const int L = A.row_len[r];
         const int64_t base = A.chunk_ptr[c] + (r - c * C);
         TX acc = TX(0);
-        for (int s = 0; s < L; ++s) {
+        int s = 0;
+        for (; s + 4 <= L; s += 4) {  // four entries' loads, then their gathers, back to back
+            const int64_t e = base + (int64_t)s * C;
+            const int c0 = __ldg(A.col + e), c1 = __ldg(A.col + e + C), c2 = __ldg(A.col + e + 2 * C),
+                      c3 = __ldg(A.col + e + 3 * C);
+            const TX v0 = (TX)ld_val(val + e), v1 = (TX)ld_val(val + e + C), v2 = (TX)ld_val(val + e + 2 * C),
+                     v3 = (TX)ld_val(val + e + 3 * C);
+            const TX p0 = P[(int64_t)c0 * k + j], p1 = P[(int64_t)c1 * k + j], p2 = P[(int64_t)c2 * k + j],
+                     p3 = P[(int64_t)c3 * k + j];
+            acc += v0 * p0;
+            acc += v1 * p1;
+            acc += v2 * p2;
+            acc += v3 * p3;
+        }
+        for (; s < L; ++s) {
             const int64_t e = base + (int64_t)s * C;
             acc += (TX)ld_val(val + e) * P[(int64_t)__ldg(A.col + e) * k + j];
         }
@@ -126,13 +140,30 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
         double rz = 0.0, rr = 0.0;
         if (on2) {
             const TX a = (TX)st.alpha[j];
-            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
-                const int64_t e = r * k + j;
-                X[e] += a * P[e];
-                const TX rv = R[e] - a * Q[e];
-                R[e] = rv;
-                rz += (double)(rv * ((TX)dinv[r] * rv));
-                rr += (double)(rv * rv);
+            constexpr int U = 4;  // rows in flight per thread
+            const int64_t step = PNT / kp;
+            for (int64_t r0 = threadIdx.x / kp; r0 < n; r0 += U * step) {
+                TX xv[U], pv[U], rv[U], qv[U], dv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t r = r0 + u * step;
+                    if (r < n) {
+                        const int64_t e = r * k + j;
+                        xv[u] = X[e]; pv[u] = P[e]; rv[u] = R[e]; qv[u] = Q[e]; dv[u] = (TX)dinv[r];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t r = r0 + u * step;
+                    if (r < n) {
+                        const int64_t e = r * k + j;
+                        X[e] = xv[u] + a * pv[u];
+                        const TX rn = rv[u] - a * qv[u];
+                        R[e] = rn;
+                        rz += (double)(rn * (dv[u] * rn));
+                        rr += (double)(rn * rn);
+                    }
+                }
             }
         }
         p_colsum(rz, kp, red, st.t0);
@@ -151,9 +182,20 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
         const bool on3 = j < k && st.run[j];
         if (on3) {
             const TX b = (TX)st.beta[j];
-            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
-                const int64_t e = r * k + j;
-                P[e] = (TX)dinv[r] * R[e] + b * P[e];
+            constexpr int U = 4;
+            const int64_t step = PNT / kp;
+            for (int64_t r0 = threadIdx.x / kp; r0 < n; r0 += U * step) {
+                TX pv[U], rv[U], dv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t r = r0 + u * step;
+                    if (r < n) { const int64_t e = r * k + j; pv[u] = P[e]; rv[u] = R[e]; dv[u] = (TX)dinv[r]; }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t r = r0 + u * step;
+                    if (r < n) P[r * k + j] = dv[u] * rv[u] + b * pv[u];
+                }
             }
         }
         __syncthreads();

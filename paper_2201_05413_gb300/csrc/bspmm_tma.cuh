@@ -30,6 +30,21 @@ template <class TX, int K> struct BSlice {
     static constexpr int R = 32 / G;                                                          // rows per pass
 };
 
+// Resident blocks per SM for width K: accumulators (K columns) + the gather
+// buffer + ~44 registers of addressing must fit 65536 / (NT x blocks).
+#ifndef GB_BSPMM_WIDE_GBUF
+#define GB_BSPMM_WIDE_GBUF 32
+#endif
+template <class TX, int K> struct BspmmOcc {
+    static constexpr int ACC = K * (int)sizeof(TX) / 4;  // accumulator registers
+    // gather buffer: 16 registers; rows of 64 bytes or more (G >= 4 lanes per
+    // row) take GB_BSPMM_WIDE_GBUF when it still fits 128 registers
+    static constexpr int GBUF =
+        (K * (int)sizeof(TX) >= 64 && ACC + GB_BSPMM_WIDE_GBUF + 44 <= 128) ? GB_BSPMM_WIDE_GBUF : 16;
+    static constexpr int R = ACC + GBUF + 44;
+    static constexpr int blocks = R <= 64 ? 4 : (R <= 84 ? 3 : 2);
+};
+
 // One warp's chunk range [c0, c1) of system S.  For each column-step of a
 // chunk the 32 rows are taken in G passes of R rows; in pass q lane l works on
 // row q R + l / G and columns (l mod G) VW .. +VW.  Returns the lane's
@@ -39,9 +54,9 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
                                                   uint64_t *bars, bool *timed_out, TX (&dot)[BSlice<TX, K>::VW]) {
     constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW, R = BSlice<TX, K>::R;
-    // (step, pass) gathers issued back to back: a buffer of at most 16 registers
+    // gathers issued back to back: a buffer of BspmmOcc<TX, K>::GBUF registers
     constexpr int RG = VW * (int)sizeof(TX) / 4;  // registers per gather
-    constexpr int GU = (16 / RG) < 1 ? 1 : 16 / RG;
+    constexpr int GU = (BspmmOcc<TX, K>::GBUF / RG) < 1 ? 1 : BspmmOcc<TX, K>::GBUF / RG;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int k = S.k;
@@ -173,6 +188,29 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
                         if (--left == 0) flush();
                     }
             }
+        } else if constexpr (GU >= G) {
+            // G lanes per row, SU = GU / G whole steps' gathers back to back
+            constexpr int SU = GU / G;
+#pragma unroll 1
+            for (int j0 = 0; j0 < sj; j0 += SU) {
+                TX pr[SU][G][VW];
+#pragma unroll
+                for (int t = 0; t < SU; ++t)
+                    if (j0 + t < sj)
+#pragma unroll
+                        for (int q = 0; q < G; ++q) ld(cs[(j0 + t) * 32 + q * R + sub], pr[t][q]);
+#pragma unroll
+                for (int t = 0; t < SU; ++t)
+                    if (j0 + t < sj) {
+#pragma unroll
+                        for (int q = 0; q < G; ++q) {
+                            const TX v = to_tx<TX>(vs[(j0 + t) * 32 + q * R + sub]);
+#pragma unroll
+                            for (int u = 0; u < VW; ++u) acc[q][u] += v * pr[t][q][u];
+                        }
+                        if (--left == 0) flush();
+                    }
+            }
         } else {
             // G lanes per row: a step's G passes, GU gathers at a time; the
             // step loop is kept rolled so the chunk end has one code path
@@ -207,13 +245,6 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
 }
 
 template <class TV> constexpr size_t bspmm_tma_smem() { return tma2_smem_bytes<TV>(); }
-
-// Resident blocks per SM for width K: accumulators (K columns) + a 16-register
-// gather buffer + ~44 registers of addressing must fit 65536 / (NT x blocks).
-template <class TX, int K> struct BspmmOcc {
-    static constexpr int R = K * (int)sizeof(TX) / 4 + 16 + 44;
-    static constexpr int blocks = R <= 64 ? 4 : (R <= 84 ? 3 : 2);
-};
 
 template <class TX, class TV, int K>
 __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))

@@ -48,7 +48,8 @@ struct SReq {
     double t_submit;
 };
 
-enum { SL_ITER = 0, SL_SERVICE = 1, SL_DONE = 2 };
+// SL_PWAIT: admitted, waiting for the next persistent launch; SL_PRUN: in one
+enum { SL_ITER = 0, SL_SERVICE = 1, SL_DONE = 2, SL_PWAIT = 3, SL_PRUN = 4 };
 
 struct Slot {
     SReq q;
@@ -85,6 +86,14 @@ struct gb_server {
     cudaStream_t main_st = nullptr, side_st = nullptr;
     cudaEvent_t ev = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing of a chunk (adaptive chunk length)
+    struct PLaunch {  // one persistent launch, on a stream of its own
+        std::vector<gb::Slot *> slots;
+        gb::BSys *d_tab = nullptr;
+        int *d_list = nullptr;
+        cudaStream_t st = nullptr;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<std::unique_ptr<PLaunch>> plaunch;
     int ips = 16;                            // iterations of the next chunk (adaptive mode)
     std::thread th;
     std::mutex mu;
@@ -219,6 +228,19 @@ static int grow(gb_server *s, T **p, size_t *cap, size_t need, cudaStream_t st) 
     return GB_OK;
 }
 
+// Requests up to n * k2 <= 2^15 (k2: the power of two >= k) are solved by one
+// block each of k_bpersist: a block works through its request at one SM's
+// pace, which for such sizes beats advancing in lock-step with the largest
+// resident requests.
+#ifndef GB_SERVE_PERSIST_LOG2
+#define GB_SERVE_PERSIST_LOG2 15
+#endif
+static bool serve_persist_eligible(int64_t n, int k, bool ru) {
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    return n * kp <= (ru ? ((int64_t)1 << GB_SERVE_PERSIST_LOG2) : PERSIST_MAX_ELEMS);
+}
+
 // --------------------------------------------------------------- admit --
 static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
     const bool ru = s->opt.precision != GB_F64;
@@ -323,45 +345,11 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
         mask[j] = ru ? 2 : 1;
         target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
     }
-    if (persist_eligible(L.n, L.k)) {
-        // small request: solved whole right here by one block of the persistent
-        // kernel; converged columns are final, any other goes on in the slot
-        // machinery from the current x
-        const int one[2] = {0, 0};  // list = {system 0 of the single-slot table}, counter
-        PersistOpts po{};
-        po.tol = s->opt.tol;
-        po.inner_tol = 1e-4;
-        po.maxit = std::min<long long>(s->opt.max_iter, 20 * (long long)L.n + 100);
-        po.max_outer = ru ? 30 : 50;
-        e = cudaMemcpyAsync(s->d_mask1, one, sizeof(one), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return fail("persist list", e);
-        ::gb::count_launches(1);
-        if (ru) k_bpersist<float><<<1, PNT, 0, st>>>(s->d_sys1, s->d_mask1, 1, s->d_mask1 + 1, po);
-        else k_bpersist<double><<<1, PNT, 0, st>>>(s->d_sys1, s->d_mask1, 1, s->d_mask1 + 1, po);
-        std::vector<int> stat(L.k);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(rr.data(), L.c.rr, sizeof(double) * L.k, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(stat.data(), L.c.status, sizeof(int) * L.k, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && ru) e = cudaMemsetAsync(L.X, 0, sizeof(float) * nk, st);  // its correction is in X64
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return fail("persistent solve", e);
-        std::vector<int> rearm(KMAX, 0);
-        std::vector<long long> it0(KMAX, 0);
-        bool left = false;
-        for (int j = 0; j < L.k; ++j) {
-            if (L.fin[j]) continue;
-            L.rel[j] = std::sqrt(rr[j] / bb[j]);
-            if (L.rel[j] <= s->opt.tol) { L.fin[j] = 1; L.fstat[j] = GB_OK; }
-            else { rearm[j] = ST_BREAK; left = true; }  // the service step re-arms it with a fresh direction
-        }
-        if (left) {
-            e = cudaMemcpyAsync(L.c.status, rearm.data(), sizeof(int) * L.k, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(L.c.it, it0.data(), sizeof(long long) * L.k, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return fail("persistent re-arm", e);
-        }
+    if (serve_persist_eligible(L.n, L.k, ru)) {
+        // small or medium request: solved whole by one block of the next
+        // persistent launch (launch_persistent), not in the lock-step loop
         L.active = 0;
-        L.state = SL_SERVICE;  // the service step retires it (or re-arms what is left)
+        L.state = SL_PWAIT;
         L.bytes = s->slot_bytes_acc;
         L.t_admit = now_ms();
         out = std::move(sl);
@@ -530,6 +518,91 @@ static int service(gb_server *s, std::vector<Slot *> &sv) {
     return GB_OK;
 }
 
+// ------------------------------------------------------ persistent lane --
+// One launch over every slot waiting for it (their initial residuals formed
+// at admission, which synchronised its stream).
+static int launch_persistent(gb_server *s) {
+    std::vector<Slot *> w;
+    for (auto &p : s->slots) if (p->state == SL_PWAIT) w.push_back(p.get());
+    if (w.empty()) return GB_OK;
+    const bool ru = s->opt.precision != GB_F64;
+    auto L = std::make_unique<gb_server::PLaunch>();
+    GB_CHECK_CUDA(cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking));
+    cudaStream_t st = L->st;
+    const int m = (int)w.size();
+    std::vector<BSys> tab;
+    std::vector<int> list(m + 1, 0);  // list, then the block counter
+    long long maxit = 1;
+    for (int i = 0; i < m; ++i) {
+        tab.push_back(desc_of(*w[i], 0));
+        list[i] = i;
+        maxit = std::max<long long>(maxit, 20 * (long long)w[i]->n + 100);
+    }
+    GB_CHECK_CUDA(cudaMallocAsync((void **)&L->d_tab, sizeof(BSys) * m, st));
+    GB_CHECK_CUDA(cudaMallocAsync((void **)&L->d_list, sizeof(int) * (m + 1), st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(L->d_tab, tab.data(), sizeof(BSys) * m, cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(L->d_list, list.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, st));
+    PersistOpts po{};
+    po.tol = s->opt.tol;
+    po.inner_tol = 1e-4;
+    po.maxit = std::min<long long>(s->opt.max_iter, maxit);
+    po.max_outer = ru ? 30 : 50;
+    const int grid = std::min(m, num_sms() * 2);
+    ::gb::count_launches(1);
+    if (ru) k_bpersist<float><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+    else k_bpersist<double><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+    GB_CHECK_CUDA(cudaGetLastError());
+    GB_CHECK_CUDA(cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming));
+    GB_CHECK_CUDA(cudaEventRecord(L->done, st));
+    for (Slot *x : w) x->state = SL_PRUN;
+    L->slots = std::move(w);
+    s->plaunch.push_back(std::move(L));
+    return GB_OK;
+}
+
+// Finished persistent launches: converged columns are final; any other column
+// is re-armed with a fresh direction by the service step and goes on in the
+// lock-step loop from the current x.  Returns whether one finished.
+static int poll_persistent(gb_server *s, bool *finished) {
+    *finished = false;
+    const bool ru = s->opt.precision != GB_F64;
+    for (size_t li = 0; li < s->plaunch.size();) {
+        auto &L = s->plaunch[li];
+        const cudaError_t q = cudaEventQuery(L->done);
+        if (q == cudaErrorNotReady) { ++li; continue; }
+        GB_CHECK_CUDA(q);
+        for (Slot *x : L->slots) {
+            Slot &S = *x;
+            std::vector<double> rr(S.k), bb(S.k);
+            GB_CHECK_CUDA(cudaMemcpy(rr.data(), S.c.rr, sizeof(double) * S.k, cudaMemcpyDeviceToHost));
+            GB_CHECK_CUDA(cudaMemcpy(bb.data(), S.c.bb, sizeof(double) * S.k, cudaMemcpyDeviceToHost));
+            std::vector<int> rearm(S.k, 0);
+            std::vector<long long> it0(S.k, 0);
+            bool left = false;
+            for (int j = 0; j < S.k; ++j) {
+                if (S.fin[j]) continue;
+                S.rel[j] = bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0;
+                if (S.rel[j] <= s->opt.tol) { S.fin[j] = 1; S.fstat[j] = GB_OK; }
+                else { rearm[j] = ST_BREAK; left = true; }  // the service step re-arms it with a fresh direction
+            }
+            if (left) {
+                GB_CHECK_CUDA(cudaMemcpy(S.c.status, rearm.data(), sizeof(int) * S.k, cudaMemcpyHostToDevice));
+                GB_CHECK_CUDA(cudaMemcpy(S.c.it, it0.data(), sizeof(long long) * S.k, cudaMemcpyHostToDevice));
+                if (ru) GB_CHECK_CUDA(cudaMemset(S.X, 0, sizeof(float) * (size_t)S.n * S.k));  // its correction is in X64
+            }
+            S.active = 0;
+            S.state = SL_SERVICE;
+        }
+        cudaFreeAsync(L->d_tab, L->st);
+        cudaFreeAsync(L->d_list, L->st);
+        cudaEventDestroy(L->done);
+        cudaStreamDestroy(L->st);
+        s->plaunch.erase(s->plaunch.begin() + li);
+        *finished = true;
+    }
+    return GB_OK;
+}
+
 // ---------------------------------------------------------------- loop --
 static void server_loop(gb_server *s) {
     cudaSetDevice(s->dev);
@@ -627,6 +700,11 @@ static void server_loop(gb_server *s) {
             s->slots.push_back(std::move(sl));
             s->pending.pop_front();
         }
+        // B'. one persistent launch for the requests admitted to that lane
+        {
+            const int rc = launch_persistent(s);
+            if (rc != GB_OK) { s->fatal = rc; s->fatal_msg = gbpcg_last_error(); break; }
+        }
         // C. wait for the chunk, pull the column states of the slots in it
         if (launched) {
             cudaError_t e = cudaEventSynchronize(s->ev);
@@ -656,6 +734,18 @@ static void server_loop(gb_server *s) {
             }
             if (e != cudaSuccess) { s->fatal = GB_ECUDA; s->fatal_msg = cudaGetErrorString(e); break; }
         }
+        // C'. persistent launches that have finished
+        bool pdone = false;
+        {
+            const int rc = poll_persistent(s, &pdone);
+            if (rc != GB_OK) { s->fatal = rc; s->fatal_msg = gbpcg_last_error(); break; }
+        }
+        if (!launched && !pdone && !s->plaunch.empty()) {
+            // only persistent launches in flight: poll them gently
+            bool serviceable = false;
+            for (auto &p : s->slots) serviceable |= p->state == SL_SERVICE;
+            if (!serviceable) std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
         // D. service slots whose columns all stopped; E. drop retired slots
         std::vector<Slot *> sv;
         for (auto &p : s->slots) if (p->state == SL_SERVICE) sv.push_back(p.get());
@@ -670,7 +760,17 @@ static void server_loop(gb_server *s) {
             s->stats.mem_peak = (double)s->peak;
         }
     }
-    // fatal error or stop: fail whatever is left
+    // fatal error or stop: fail whatever is left (after any persistent launch
+    // still using the slots' buffers has finished)
+    cudaStreamSynchronize(s->main_st);
+    for (auto &L : s->plaunch) {
+        cudaStreamSynchronize(L->st);
+        cudaFreeAsync(L->d_tab, L->st);
+        cudaFreeAsync(L->d_list, L->st);
+        cudaEventDestroy(L->done);
+        cudaStreamDestroy(L->st);
+    }
+    s->plaunch.clear();
     for (auto &p : s->slots) { finish(s, p->q, s->fatal ? s->fatal : GB_EINVAL, p.get()); release_slot(s, *p); }
     s->slots.clear();
     for (auto &q : s->pending) finish(s, q, s->fatal ? s->fatal : GB_EINVAL, nullptr);
