@@ -89,7 +89,6 @@ static const int KUHN[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0
 
 orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uint64_t seed) {
     if ((dim != 2 && dim != 3) || (degree != 1 && degree != 2) || cells < 1) return NULL;
-    if (dim == 3 && jitter) return NULL; /* 3D meshes are regular Kuhn lattices */
     orc_sys *s = (orc_sys *)calloc(1, sizeof(orc_sys));
     s->dim = dim; s->degree = degree; s->cells = cells; s->jitter = jitter;
     s->diag_mode = diag_mode; s->seed = seed;
@@ -104,11 +103,14 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
     s->nel = ncell * (dim == 2 ? 2 : 6);
 
     /* vertex coordinates: lattice point i/cells, interior points of a jittered
-     * mesh moved by (2u-1)*0.25h per coordinate, u from streams 0 (x) and 1 (y),
-     * counter = vertex id. */
+     * mesh moved by (2u-1)*q per coordinate, u from streams 0 (x), 1 (y) and
+     * 3 (z), counter = vertex id; q = h/4 in 2D and h/8 in 3D, the largest
+     * amplitude h/2^m at which no Kuhn tetrahedron can invert (at h/4 one can:
+     * the determinant of its edge vectors reaches -h^3/2 over the corners of
+     * the jitter box, against >= h^3/4 at h/8). */
     s->vx = (double *)malloc(sizeof(double) * s->nv * dim);
-    const uint64_t kx = orc_rng_key(seed, 0), ky = orc_rng_key(seed, 1);
-    const double q = 0.25 / (double)cells;
+    const uint64_t keys[3] = {orc_rng_key(seed, 0), orc_rng_key(seed, 1), orc_rng_key(seed, 3)};
+    const double q = (dim == 3 ? 0.125 : 0.25) / (double)cells;
     for (int64_t v = 0; v < s->nv; ++v) {
         int64_t t = v;
         int idx[3] = {0, 0, 0};
@@ -117,8 +119,8 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
         for (int d = 0; d < dim; ++d) if (idx[d] == 0 || idx[d] == cells) interior = 0;
         for (int d = 0; d < dim; ++d) {
             double x = (double)idx[d] / (double)cells;
-            if (jitter && interior && d < 2) {
-                uint64_t r = orc_rng_u64(d == 0 ? kx : ky, (uint64_t)v);
+            if (jitter && interior) {
+                uint64_t r = orc_rng_u64(keys[d], (uint64_t)v);
                 double dd = 2.0 * u01(r) - 1.0;
                 x = x + dd * q;
             }

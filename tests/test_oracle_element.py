@@ -41,11 +41,12 @@ def test_p1_2d_cotangent_weights():
 
 
 # ----------------------------------------------------------------- P1, 3D --
-def test_p1_3d_cotangent_weights():
+@pytest.mark.parametrize("jitter", [0, 1])
+def test_p1_3d_cotangent_weights(jitter):
     """Sec. 2.2: w(i,j) = (1/6) sum_k l_k cot(alpha_k), l_k the length of the edge
     opposite (i,j) in tet k and alpha_k the dihedral angle at that edge;
     the per-tet stiffness off-diagonal is -(1/6) l cot(alpha)."""
-    s = O.System(3, 1, 3)
+    s = O.System(3, 1, 3, jitter=jitter, seed=8)
     for e in range(s.n_elements):
         P = _vertex_ids(s, e)
         K = s.element_matrix(e)
@@ -119,7 +120,8 @@ def _stiffness_by_quadrature(nodes, P, deg):
     return K
 
 
-@pytest.mark.parametrize("dim,degree,jitter", [(2, 1, 1), (2, 2, 1), (2, 2, 0), (3, 1, 0), (3, 2, 0)])
+@pytest.mark.parametrize("dim,degree,jitter", [(2, 1, 1), (2, 2, 1), (2, 2, 0), (3, 1, 0), (3, 2, 0), (3, 1, 1),
+                                               (3, 2, 1)])
 def test_element_matrix_vs_lagrange_quadrature(dim, degree, jitter):
     s = O.System(dim, degree, 3, jitter=jitter, diag_mode=1, seed=21)
     X = s.dof_coords()

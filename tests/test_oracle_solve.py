@@ -34,6 +34,8 @@ def test_cfg1_closed_form():
     (3, 1, 6, 0, O.G_X2_Y2_2Z2, None),                       # Kuhn 7-point exact on quadratics
     (3, 2, 4, 0, O.G_X2_Y2_2Z2, None),                       # P2 exact on quadratics
     (3, 1, 5, 0, O.G_LINEAR, [1.0, -0.5, 0.25, 2.0]),
+    (3, 1, 6, 1, O.G_LINEAR, [1.0, -0.5, 0.25, 2.0]),       # jittered 3D: P1 exact on linear data
+    (3, 2, 4, 1, O.G_X2_Y2_2Z2, None),                       # jittered 3D: P2 exact on quadratics
 ])
 def test_exact_reproduction(dim, deg, cells, jit, gid, coef):
     s, b, x, info = O.solve_system(dim, deg, cells, jitter=jit, diag_mode=1, seed=3, gid=gid,
