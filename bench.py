@@ -45,7 +45,7 @@ ITERS_FULL = [3597, 8534]
 # of each kernel on this workload (ncu --set full, one launch after a warm-up
 # launch, `--profile-kernels p2`); None whenever the kernel changes until it is
 # captured again
-NCU_TRAFFIC = {"k_spmv_tma2<double,double>": 640554496, "k_spmv_tma2<float,float>": 423282688}
+NCU_TRAFFIC = {"k_spmv_tma2<double,double>": 640554496, "k_spmv_tma2<float,float>": 423162112}
 WORKLOAD = "cfg2: 2D unit square 1024x1024 cells, jittered +-h/4, random diagonals (seed 1), P1 + P2, g=x^2-y^2"
 
 
@@ -497,6 +497,8 @@ EPS_SYSTEMS = [  # (name, spec, gid, closed form available)
     ("2D-P2-jittered-1024", (2, 2, 1024, 1, 1, 1), 1, True),
     ("3D-P1-Kuhn-128", (3, 1, 128, 0, 0, 0), 2, True),
     ("3D-P2-Kuhn-64", (3, 2, 64, 0, 0, 0), 2, True),
+    ("3D-P1-Kuhn-jittered-128", (3, 1, 128, 1, 0, 7), 2, False),  # irregular tets: P1 not exact on quadratics
+    ("3D-P2-Kuhn-jittered-64", (3, 2, 64, 1, 0, 7), 2, True),
 ]
 
 

@@ -68,18 +68,20 @@ typedef struct gb_allocator {
  * SW-NE diagonal, or by a per-cell random diagonal (diag_mode 1: the NW-SE one
  * when the cell's draw is below 1/2); with jitter=1 every interior vertex moves
  * by (2u-1)h/4 per coordinate.  3D: Kuhn split of each cube into six
- * tetrahedra along its main diagonal (jitter must be 0).  The draws u come
- * from the counter-based SplitMix64 generator: output i of stream s of run
- * `seed` is mix64(key + (i+1)*0x9E3779B97F4A7C15), key = seed*2^40 xor s*2^32,
- * u = (output >> 11) * 2^-53; stream 0/1 jitter x/y (i = vertex id), stream 2
- * the diagonal (i = cell id).  degree 1 (P1) or 2 (P2, Sec. 4.2 / Table 7):
+ * tetrahedra along its main diagonal (diag_mode must be 0); with jitter=1 every
+ * interior vertex moves by (2u-1)h/8 per coordinate (at h/4 a tetrahedron
+ * could invert) -- an irregular tetrahedral mesh.  The draws u come from the
+ * counter-based SplitMix64 generator: output i of stream s of run `seed` is
+ * mix64(key + (i+1)*0x9E3779B97F4A7C15), key = seed*2^40 xor s*2^32,
+ * u = (output >> 11) * 2^-53; streams 0/1/3 jitter x/y/z (i = vertex id),
+ * stream 2 the diagonal (i = cell id).  degree 1 (P1) or 2 (P2, Sec. 4.2 / Table 7):
  * dofs are the points of the lattice with degree*cells+1 points per side;
  * boundary dofs are those with a coordinate 0 or degree*cells. */
 typedef struct gb_fem_spec {
     int32_t dim;        /* 2 or 3 */
     int32_t degree;     /* 1 or 2 */
     int32_t cells;      /* cells per side, >= 2 */
-    int32_t jitter;     /* 0 or 1 (2D only) */
+    int32_t jitter;     /* 0 or 1 */
     int32_t diag_mode;  /* 0 fixed SW-NE, 1 random per cell (2D only) */
     int32_t reserved;   /* must be 0 */
     uint64_t seed;

@@ -192,6 +192,7 @@ static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions 
 extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
                                  double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                                  PcgStats *stats) {
+    gb::Range range("gbpcg:pcg_solve_batched");
     GB_REQUIRE(nsys >= 1 && A && d_B && d_X && k && stats, "pcg_solve_batched: NULL argument");
     for (int s = 0; s < nsys; ++s) {
         GB_REQUIRE(A[s] && d_B[s] && d_X[s], "pcg_solve_batched: system %d has a NULL pointer", s);

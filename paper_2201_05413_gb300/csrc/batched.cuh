@@ -687,10 +687,10 @@ static inline int units_of_rows(int64_t n, int64_t *rows_per_unit) {
 // Widest width class (0: k = 1 .. 5: k <= 32) that takes the TMA-streamed SpMM;
 // wider classes take the general kernel, whose lane groups gather a P row as
 // one coalesced segment.  Measured on 2D P2 1024^2 (SpMM ms, TMA / general):
-// fp32 k=1 0.16/0.27, k=8 0.32/0.43, k=16 0.49/0.71, k=32 1.17/1.09;
-// fp64 k=1 0.21/0.30, k=8 0.86/0.94, k=16 1.83/1.80, k=32 4.00/3.52.
+// fp32 k=1 0.16/0.27, k=8 0.31/0.43, k=16 0.48/0.71, k=32 0.92/1.09 (2048^2:
+// 3.36/4.31); fp64 k=1 0.21/0.30, k=8 0.86/0.94, k=16 1.83/1.80, k=32 4.00/3.52.
 #ifndef GB_BSPMM_TMA_MAXC32
-#define GB_BSPMM_TMA_MAXC32 4
+#define GB_BSPMM_TMA_MAXC32 5
 #endif
 #ifndef GB_BSPMM_TMA_MAXC64
 #define GB_BSPMM_TMA_MAXC64 3

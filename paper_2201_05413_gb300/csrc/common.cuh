@@ -9,9 +9,20 @@
 #include <cstdio>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gbpcg.h"
 
 namespace gb {
+
+// NVTX range over one library phase (assembly, SELL build, a solve, a serving
+// chunk): profilers (nsys, ncu --nvtx) attribute the kernels to the phase.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // ---------------------------------------------------------------- errors --
 void set_error(const char *fmt, ...);
@@ -98,6 +109,8 @@ int num_sms();
 #define GB_TMA_BLOCKS_PER_SM 4
 #endif
 constexpr int TMA_BLOCKS_PER_SM = GB_TMA_BLOCKS_PER_SM;
+// the fp32/bf16 SpMV (smaller shared-memory ring) runs 5 blocks per SM
+constexpr int TMA_BLOCKS_PER_SM_NARROW = 5;
 // Grid for a grid-stride kernel: a multiple of the SM count, at most `want`.
 inline int stride_grid(int64_t work_items, int block, int per_sm) {
     int sms = num_sms();

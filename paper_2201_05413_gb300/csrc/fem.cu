@@ -32,8 +32,8 @@ static inline uint64_t stream_key(uint64_t seed, uint32_t stream) {
 
 struct MeshDev {
     int dim, deg, cells, S, V, jitter, diag_mode;
-    uint64_t kx, ky, kf;
-    double q;  // jitter amplitude h/4
+    uint64_t kx, ky, kz, kf;
+    double q;  // jitter amplitude: h/4 in 2D, h/8 in 3D
 };
 
 // 2D triangles of a cell as vertex offsets (dx, dy): [flip][tri][vertex].
@@ -51,17 +51,19 @@ __device__ __forceinline__ bool cell_flipped(const MeshDev &m, int64_t cell) {
     return m.diag_mode == 1 && (sm_draw(m.kf, (uint64_t)cell) >> 63) == 0;
 }
 
-// Coordinate of vertex v = (i,j[,k]) along `axis`: i/cells, moved by
-// (2u-1)h/4 on interior vertices of a jittered mesh.  Correctly rounded basic
-// operations with no contraction, so the value is reproducible exactly.
+// Coordinate of vertex v = (i,j[,k]) along `axis`: i/cells, moved by (2u-1)q
+// on interior vertices of a jittered mesh (q = h/4 in 2D; h/8 in 3D, where a
+// Kuhn tetrahedron could invert at h/4), u from stream 0, 1 or 3 for x, y, z.
+// Correctly rounded basic operations with no contraction, so the value is
+// reproducible exactly.
 __device__ __forceinline__ double vertex_coord(const MeshDev &m, const int *vi, int axis) {
     double x = __ddiv_rn((double)vi[axis], (double)m.cells);
-    if (m.jitter && axis < 2) {
+    if (m.jitter) {
         bool interior = true;
         for (int d = 0; d < m.dim; ++d) interior &= (vi[d] > 0 && vi[d] < m.cells);
         if (interior) {
             int64_t vid = vi[0] + (int64_t)m.V * (vi[1] + (m.dim == 3 ? (int64_t)m.V * vi[2] : 0));
-            uint64_t r = sm_draw(axis == 0 ? m.kx : m.ky, (uint64_t)vid);
+            uint64_t r = sm_draw(axis == 0 ? m.kx : (axis == 1 ? m.ky : m.kz), (uint64_t)vid);
             double u = __dmul_rn((double)(r >> 11), 0x1p-53);
             double d = __dsub_rn(__dmul_rn(2.0, u), 1.0);
             x = __dadd_rn(x, __dmul_rn(d, m.q));
@@ -514,6 +516,7 @@ static int assemble_impl(gb_fem_system *s, cudaStream_t st) {
 
 extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, void *stream,
                             gb_fem_system **out) {
+    gb::Range range("gbpcg:fem_assemble");
     GB_REQUIRE(spec && out, "fem_assemble: NULL argument");
     *out = nullptr;
     GB_REQUIRE(spec->dim == 2 || spec->dim == 3, "fem_assemble: dim must be 2 or 3");
@@ -521,8 +524,8 @@ extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, 
     GB_REQUIRE(spec->cells >= 2, "fem_assemble: cells must be >= 2");
     GB_REQUIRE(spec->jitter == 0 || spec->jitter == 1, "fem_assemble: jitter must be 0 or 1");
     GB_REQUIRE(spec->diag_mode == 0 || spec->diag_mode == 1, "fem_assemble: diag_mode must be 0 or 1");
-    GB_REQUIRE(spec->dim == 2 || (spec->jitter == 0 && spec->diag_mode == 0),
-               "fem_assemble: 3D meshes are regular Kuhn lattices (jitter=0, diag_mode=0)");
+    GB_REQUIRE(spec->dim == 2 || spec->diag_mode == 0,
+               "fem_assemble: 3D meshes use the Kuhn split of every cube (diag_mode=0)");
     GB_REQUIRE(spec->reserved == 0, "fem_assemble: reserved must be 0");
     const int64_t S = (int64_t)spec->degree * spec->cells + 1;
     int64_t n_dof = 1, n_free = 1;
@@ -539,7 +542,8 @@ extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, 
     m.dim = spec->dim; m.deg = spec->degree; m.cells = spec->cells; m.S = (int)S; m.V = spec->cells + 1;
     m.jitter = spec->jitter; m.diag_mode = spec->diag_mode;
     m.kx = stream_key(spec->seed, 0); m.ky = stream_key(spec->seed, 1); m.kf = stream_key(spec->seed, 2);
-    m.q = 0.25 / (double)spec->cells;
+    m.kz = stream_key(spec->seed, 3);
+    m.q = (spec->dim == 3 ? 0.125 : 0.25) / (double)spec->cells;
     s->n_dof = n_dof; s->n_free = n_free; s->n_bnd = n_dof - n_free;
     int rc;
     if (m.dim == 2) rc = m.deg == 1 ? assemble_impl<2, 1>(s, st) : assemble_impl<2, 2>(s, st);

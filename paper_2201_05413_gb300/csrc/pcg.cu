@@ -27,7 +27,8 @@ namespace gb {
 // q = A p with TMA-staged slices (spmv_tma.cuh), one warp per balanced chunk
 // range, then the same p.q reduction and alpha as k_spmv_pq.
 template <class TV, class TX, class TI>
-__global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restrict__ val,
+__global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const int32_t *__restrict__ wchunk,
+                                                 const TV *__restrict__ val,
                                                  const TX *__restrict__ p, TX *__restrict__ q,
                                                  double *partials, PcgScal *S) {
     if (S->done) {
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const TV *__restric
     }
     __syncwarp();
     const int gw = blockIdx.x * TMA_WARPS + warp;
-    const int c0 = __ldg(A.warp_chunk + gw), c1 = __ldg(A.warp_chunk + gw + 1);
+    const int c0 = __ldg(wchunk + gw), c1 = __ldg(wchunk + gw + 1);
     bool timed_out = false;
     const TX dot = spmv_warp_stream<TV, TX, NB, TI>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
     if (timed_out && lane == 0) atomicExch(&S->err, 1);
@@ -74,15 +75,21 @@ static void launch_spmv_tma_t(const SellView &A, const TV *val, const TX *p, TX 
         cudaFuncSetAttribute(k_spmv_tma<TV, TX, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    ::gb::count_launches(1); k_spmv_tma<TV, TX, TI><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+    // the warp partition of k_spmv_tma2 for the same value type, so that both
+    // index widths sum p.q in the same order
+    const bool narrow = sizeof(TV) < 8 && A.warp_chunk5;
+    const int32_t *wchunk = narrow ? A.warp_chunk5 : A.warp_chunk;
+    const int grid = (narrow ? A.nwarps5 : A.nwarps) / TMA_WARPS;
+    ::gb::count_launches(1); k_spmv_tma<TV, TX, TI><<<grid, NT, smem, st>>>(A, wchunk, val, p, q, partials, S);
 }
 
 // q = A p with the second streaming loop (32-bit indices, spmv_tma.cuh), one
 // warp per balanced chunk range, then the p.q reduction and alpha.
 template <class TV, class TX>
-__global__ void __launch_bounds__(NT) k_spmv_tma2(SellView A, const TV *__restrict__ val,
-                                                  const TX *__restrict__ p, TX *__restrict__ q,
-                                                  double *partials, PcgScal *S) {
+__global__ void __launch_bounds__(NT, (sizeof(TV) < 8 ? TMA_BLOCKS_PER_SM_NARROW : TMA_BLOCKS_PER_SM))
+    k_spmv_tma2(SellView A, const int32_t *__restrict__ wchunk,
+                                                  const TV *__restrict__ val, const TX *__restrict__ p,
+                                                  TX *__restrict__ q, double *partials, PcgScal *S) {
     if (S->done) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && S->use_cond) cudaGraphSetConditional(S->cond, 0);
         return;
@@ -100,7 +107,7 @@ __global__ void __launch_bounds__(NT) k_spmv_tma2(SellView A, const TV *__restri
     }
     __syncwarp();
     const int gw = blockIdx.x * TMA_WARPS + warp;
-    const int c0 = __ldg(A.warp_chunk + gw), c1 = __ldg(A.warp_chunk + gw + 1);
+    const int c0 = __ldg(wchunk + gw), c1 = __ldg(wchunk + gw + 1);
     bool timed_out = false;
     const TX dot = spmv_warp_stream2<TV, TX>(A, val, p, q, c0, c1, bufs[warp], &bars[NB * warp], &timed_out);
     if (timed_out && lane == 0) atomicExch(&S->err, 1);
@@ -127,7 +134,11 @@ static void launch_spmv_tma2(const SellView &A, const TV *val, const TX *p, TX *
         cudaFuncSetAttribute(k_spmv_tma2<TV, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    ::gb::count_launches(1); k_spmv_tma2<TV, TX><<<A.nwarps / TMA_WARPS, NT, smem, st>>>(A, val, p, q, partials, S);
+    // fp64 (48 KB ring per block): 4 blocks per SM; fp32/bf16: 5 blocks per SM
+    const bool narrow = sizeof(TV) < 8 && A.warp_chunk5;
+    const int32_t *wchunk = narrow ? A.warp_chunk5 : A.warp_chunk;
+    const int grid = (narrow ? A.nwarps5 : A.nwarps) / TMA_WARPS;
+    ::gb::count_launches(1); k_spmv_tma2<TV, TX><<<grid, NT, smem, st>>>(A, wchunk, val, p, q, partials, S);
 }
 
 // 16-bit column deltas when the matrix has them (first streaming loop), 32-bit
@@ -638,7 +649,7 @@ static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &
 // partial-sum slots every solver kernel may write (2 per block of the largest grid)
 static size_t partial_slots(const gb_sell *A, const Grids &g) {
     int blocks = std::max(g.spmv, g.vec);
-    if (A->warp_chunk) blocks = std::max(blocks, A->nwarps / TMA_WARPS);
+    if (A->warp_chunk) blocks = std::max(blocks, std::max(A->nwarps, A->nwarps5) / TMA_WARPS);
     return 3 * (size_t)blocks;
 }
 
@@ -940,6 +951,7 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
 
 extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
                          void *stream, PcgStats *stats) {
+    gb::Range range("gbpcg:pcg_solve");
     GB_REQUIRE(A && d_b && d_x, "pcg_solve: NULL argument");
     PcgStats dummy{};
     if (!stats) stats = &dummy;

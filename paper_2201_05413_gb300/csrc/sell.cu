@@ -273,6 +273,10 @@ static int build_sell(int64_t n, const int32_t *rp, const int32_t *ci, const dou
         STEP(mem.alloc_n(&A->warp_chunk, (size_t)A->nwarps + 1));
         ::gb::count_launches(1); k_warp_partition<<<stride_grid(A->nwarps + 1, 256, 4), 256, 0, st>>>(
             A->nchunks, A->chunk_ptr, padded, A->nwarps, A->warp_chunk);
+        A->nwarps5 = num_sms() * TMA_BLOCKS_PER_SM_NARROW * 8;
+        STEP(mem.alloc_n(&A->warp_chunk5, (size_t)A->nwarps5 + 1));
+        ::gb::count_launches(1); k_warp_partition<<<stride_grid(A->nwarps5 + 1, 256, 4), 256, 0, st>>>(
+            A->nchunks, A->chunk_ptr, padded, A->nwarps5, A->warp_chunk5);
         STEPC(cudaGetLastError());
     }
     STEPC(cudaStreamSynchronize(st));
@@ -333,6 +337,7 @@ using namespace gb;
 
 extern "C" int csr_to_sell(const gb_fem_system *sys, int C, int sigma, int val_types,
                            const gb_allocator *alloc, void *stream, gb_sell **out) {
+    gb::Range range("gbpcg:csr_to_sell");
     GB_REQUIRE(sys, "csr_to_sell: NULL system");
     int64_t n;
     const int32_t *rp, *col;
@@ -345,6 +350,7 @@ extern "C" int csr_to_sell(const gb_fem_system *sys, int C, int sigma, int val_t
 extern "C" int csr_to_sell_raw(int64_t n, const int32_t *d_rowptr, const int32_t *d_col,
                                const double *d_val, int C, int sigma, int val_types,
                                const gb_allocator *alloc, void *stream, gb_sell **out) {
+    gb::Range range("gbpcg:csr_to_sell");
     GB_REQUIRE(d_rowptr && d_col && d_val, "csr_to_sell_raw: NULL array");
     return build_sell(n, d_rowptr, d_col, d_val, nullptr, 0, C, sigma, val_types, alloc,
                       (cudaStream_t)stream, out);
@@ -384,7 +390,7 @@ extern "C" void sell_destroy(gb_sell *A) {
     Mem &m = A->mem;
     m.release(A->perm); m.release(A->iperm); m.release(A->row_len);
     m.release(A->dinv); m.release(A->dinv32);
-    m.release(A->chunk_w); m.release(A->chunk_ptr); m.release(A->warp_chunk);
+    m.release(A->chunk_w); m.release(A->chunk_ptr); m.release(A->warp_chunk); m.release(A->warp_chunk5);
     m.release(A->col); m.release(A->col16); m.release(A->val); m.release(A->val32); m.release(A->val16);
     delete A;
 }

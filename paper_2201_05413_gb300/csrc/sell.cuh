@@ -22,6 +22,8 @@ struct SellView {
     const int32_t *warp_chunk;  // nwarps+1 chunk bounds, balanced by padded nonzeros (C == 32)
     int nwarps;
     const int16_t *col16;       // column - min(row, n-1) per padded slot, or null (C == 32)
+    const int32_t *warp_chunk5; // the same for the 5-blocks-per-SM grid of the fp32/bf16 SpMV
+    int nwarps5;
 };
 
 }  // namespace gb
@@ -30,9 +32,9 @@ struct gb_sell {
     int64_t n = 0, nnz = 0, padded = 0, nchunks = 0;
     int C = 32, sigma = 1, max_row = 0;
     int32_t *perm = nullptr, *iperm = nullptr, *row_len = nullptr, *chunk_w = nullptr, *col = nullptr;
-    int32_t *warp_chunk = nullptr;
+    int32_t *warp_chunk = nullptr, *warp_chunk5 = nullptr;
     int16_t *col16 = nullptr;
-    int nwarps = 0;
+    int nwarps = 0, nwarps5 = 0;
     int variant_hint = 0;  // SpMV variant solves use by default (set by sell_autotune)
     double dinv_max = 0.0; // max_i 1/K_ii (host copy)
     int64_t *chunk_ptr = nullptr;
@@ -42,6 +44,6 @@ struct gb_sell {
     gb::Mem mem;
     gb::SellView view() const {
         return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32,
-                            chunk_w, warp_chunk, nwarps, col16};
+                            chunk_w, warp_chunk, nwarps, col16, warp_chunk5, nwarps5};
     }
 };

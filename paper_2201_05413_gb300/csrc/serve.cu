@@ -618,6 +618,7 @@ static void server_loop(gb_server *s) {
             }
         }
         // A. launch a chunk of CG iterations for the iterating slots (main stream)
+        gb::Range round_range("gbpcg:serve_round");
         std::vector<Slot *> it_slots;
         for (auto &p : s->slots) if (p->state == SL_ITER) it_slots.push_back(p.get());
         // the table in width-class order: each class's units are contiguous

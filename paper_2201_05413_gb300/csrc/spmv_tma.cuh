@@ -259,7 +259,7 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
 #define GB_TMA2_SJ32 8
 #endif
 #ifndef GB_TMA2_NB32
-#define GB_TMA2_NB32 3
+#define GB_TMA2_NB32 2
 #endif
 #ifndef GB_TMA2_SJ64
 #define GB_TMA2_SJ64 8

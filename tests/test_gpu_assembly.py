@@ -20,6 +20,8 @@ CASES = [  # dim, degree, cells, jitter, diag_mode, seed
     (2, 2, 24, 0, 1, 7),
     (3, 1, 7, 0, 0, 0),
     (3, 2, 5, 0, 0, 0),
+    (3, 1, 6, 1, 0, 9),       # jittered 3D (irregular tetrahedra)
+    (3, 2, 4, 1, 0, 10),
 ]
 
 VAL_RTOL = 1e-13
@@ -155,7 +157,7 @@ def test_bad_specs_raise(P):
     with pytest.raises(P.GbError):
         P.FemSystem(4, 1, 8)
     with pytest.raises(P.GbError):
-        P.FemSystem(3, 1, 8, jitter=1)
+        P.FemSystem(3, 1, 8, jitter=1, diag_mode=1)  # 3D: the Kuhn split only
     with pytest.raises(P.GbError):
         P.FemSystem(2, 3, 8)
     with pytest.raises(P.GbError):

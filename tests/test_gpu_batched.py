@@ -30,7 +30,7 @@ def _oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k):
 
 
 @pytest.mark.parametrize("persist_off", [0, 1])
-@pytest.mark.parametrize("k", [1, 3, 8, 32])
+@pytest.mark.parametrize("k", [1, 3, 8, 12, 16, 32])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_multi_rhs_matches_oracle(P, k, prec, persist_off):
     spec = (2, 2, 24, 1, 1, 2)

@@ -46,6 +46,7 @@ def _solve_both(P, dim, deg, cells, jit, dm, seed, gid, coef=None, C=32, sigma=2
     (2, 2, 48, 1, 1, 1, O.G_X2_Y2),
     (3, 1, 20, 0, 0, 0, O.G_X2_Y2_2Z2),
     (3, 2, 10, 0, 0, 0, O.G_X2_Y2_2Z2),
+    (3, 1, 20, 1, 0, 2, O.G_X2_Y2_2Z2),     # jittered 3D P1: no closed form, oracle solve
 ])
 def test_fp64_pcg_matches_oracle(P, case):
     d, s, xd, xo, st, ito, relres = _solve_both(P, *case)
@@ -70,6 +71,7 @@ def test_cfg1_closed_form(P):
     (2, 2, 40, 1, 1, 4, O.G_X2_Y2),         # P2 reproduces x^2 - y^2
     (3, 1, 16, 0, 0, 0, O.G_X2_Y2_2Z2),     # Kuhn 7-point reproduces quadratics
     (3, 2, 8, 0, 0, 0, O.G_X2_Y2_2Z2),
+    (3, 2, 8, 1, 0, 3, O.G_X2_Y2_2Z2),      # jittered 3D: P2 reproduces quadratics
 ])
 def test_exact_polynomial_reproduction(P, case):
     dim, deg, cells, jit, dm, seed, gid = case
