@@ -66,6 +66,12 @@ def lib():
         L.orc_pcg.restype = C.c_int
         L.orc_pcg.argtypes = [C.c_int64, i64p, i32p, f64p, f64p, f64p, C.c_double, C.c_int64,
                               i64p, f64p]
+        L.orc_pcg_bj.restype = C.c_int
+        L.orc_pcg_bj.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p, f64p, C.c_double,
+                                 C.c_int64, i64p, f64p]
+        L.orc_bjacobi.restype = C.c_int
+        L.orc_bjacobi.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p]
+        L.orc_bjacobi_apply.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [C.c_int64, i64p, i32p, f64p, f64p, f64p]
         L.orc_sell_size.argtypes = [C.c_int64, i64p, C.c_int, C.c_int, i64p, i64p]
@@ -201,18 +207,42 @@ def spmv(rp, ci, v, x):
     return y
 
 
-def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None):
-    """Jacobi-PCG to ||b-Ax||/||b|| <= tol (Eq. 2).  Returns (x, status, iters, relres)."""
+def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None):
+    """PCG to ||b-Ax||/||b|| <= tol (Eq. 2) with the Jacobi preconditioner, or
+    with block-Jacobi over blocks of bs consecutive rows when bs is given.
+    Returns (x, status, iters, relres)."""
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     it = np.zeros(1, np.int64)
     rr = np.zeros(1)
     maxit = 20 * n + 100 if maxit is None else maxit
-    st = lib().orc_pcg(n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double),
-                       _p(b, C.c_double), _p(x, C.c_double), tol, maxit,
-                       _p(it, C.c_int64), _p(rr, C.c_double))
+    args = (_p(b, C.c_double), _p(x, C.c_double), tol, maxit, _p(it, C.c_int64), _p(rr, C.c_double))
+    A = (n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double))
+    st = lib().orc_pcg(*A, *args) if bs is None else lib().orc_pcg_bj(*A, int(bs), *args)
     return x, int(st), int(it[0]), float(rr[0])
+
+
+def bjacobi(rp, ci, v, bs):
+    """Block-Jacobi inverses: array (ceil(n/bs), bs, bs), a short last block in
+    its leading corner (zeros elsewhere)."""
+    n = len(rp) - 1
+    nblk = (n + bs - 1) // bs
+    W = np.zeros(max(nblk, 1) * bs * bs)
+    if lib().orc_bjacobi(n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double), int(bs),
+                         _p(W, C.c_double)):
+        raise np.linalg.LinAlgError("a diagonal block is not SPD")
+    return W[:nblk * bs * bs].reshape(nblk, bs, bs)
+
+
+def bjacobi_apply(bs, W, r):
+    """z = M^{-1} r for the block inverses W of bjacobi()."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    z = np.empty_like(r)
+    lib().orc_bjacobi_apply(len(r), int(bs), _p(W.reshape(-1), C.c_double), _p(r, C.c_double),
+                            _p(z, C.c_double))
+    return z
 
 
 def cholesky_solve(rp, ci, v, b):

@@ -533,16 +533,25 @@ static double dot(int64_t n, const double *a, const double *b) {
     return t;
 }
 
-/* Preconditioned CG (Hestenes-Stiefel) with M = diag(A):
+/* z = M^{-1} r for one preconditioner M (its data in ctx). */
+typedef void (*precond_fn)(int64_t n, const void *ctx, const double *r, double *z);
+
+/* Jacobi: M = diag(A), ctx = 1/A_ii */
+static void jacobi_apply(int64_t n, const void *ctx, const double *r, double *z) {
+    const double *dinv = (const double *)ctx;
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+}
+
+/* Preconditioned CG (Hestenes-Stiefel):
  *   r = b - A x, z = M^{-1} r, p = z, rho = r.z
  *   repeat: q = A p; alpha = rho / p.q; x += alpha p; r -= alpha q;
  *           stop if ||r|| / ||b|| <= tol (Eq. 2);
  *           z = M^{-1} r; rho' = r.z; beta = rho'/rho; p = z + beta p.
  * At a stop on the recursive residual the true residual b - A x is formed;
  * if it is above tol, r is replaced by it and the recurrence restarts. */
-int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
-            const double *b, double *x, double tol, int64_t maxit,
-            int64_t *iters, double *relres) {
+static int pcg_core(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                    precond_fn apply, const void *ctx, const double *b, double *x, double tol,
+                    int64_t maxit, int64_t *iters, double *relres) {
     *iters = 0;
     const double bn = sqrt(dot(n, b, b));
     if (bn == 0.0) {
@@ -550,16 +559,10 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
         *relres = 0.0;
         return 0;
     }
-    double *dinv = (double *)malloc(sizeof(double) * n);
     double *r = (double *)malloc(sizeof(double) * n);
     double *z = (double *)malloc(sizeof(double) * n);
     double *p = (double *)malloc(sizeof(double) * n);
     double *q = (double *)malloc(sizeof(double) * n);
-    for (int64_t i = 0; i < n; ++i) {
-        double d = 0.0;
-        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) if (ci[k] == i) d = v[k];
-        dinv[i] = 1.0 / d;
-    }
     int status = 1;
     int64_t it = 0;
     int restarts = 0;
@@ -568,7 +571,8 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     double rel = sqrt(dot(n, r, r)) / bn;
     while (status == 1) {
         if (rel <= tol) { status = 0; break; }
-        for (int64_t i = 0; i < n; ++i) { z[i] = dinv[i] * r[i]; p[i] = z[i]; }
+        apply(n, ctx, r, z);
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i];
         double rho = dot(n, r, z);
         int restart = 0;
         while (it < maxit) {
@@ -589,7 +593,7 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                 restart = 1;
                 break;
             }
-            for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            apply(n, ctx, r, z);
             const double rho1 = dot(n, r, z);
             const double beta = rho1 / rho;
             rho = rho1;
@@ -600,8 +604,54 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     }
     *iters = it;
     *relres = rel;
-    free(dinv); free(r); free(z); free(p); free(q);
+    free(r); free(z); free(p); free(q);
     return status;
+}
+
+int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+            const double *b, double *x, double tol, int64_t maxit,
+            int64_t *iters, double *relres) {
+    double *dinv = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) if (ci[k] == i) d = v[k];
+        dinv[i] = 1.0 / d;
+    }
+    const int st = pcg_core(n, rp, ci, v, jacobi_apply, dinv, b, x, tol, maxit, iters, relres);
+    free(dinv);
+    return st;
+}
+
+/* Dense A = L L^T of an m x m row-major SPD matrix, the lower triangle
+ * overwritten (textbook column-by-column form).  Returns 1 if not SPD. */
+static int dense_cholesky(int64_t m, double *L) {
+    for (int64_t j = 0; j < m; ++j) {
+        double d = L[j * m + j];
+        for (int64_t k = 0; k < j; ++k) d -= L[j * m + k] * L[j * m + k];
+        if (!(d > 0.0)) return 1;
+        d = sqrt(d);
+        L[j * m + j] = d;
+        for (int64_t i = j + 1; i < m; ++i) {
+            double t = L[i * m + j];
+            for (int64_t k = 0; k < j; ++k) t -= L[i * m + k] * L[j * m + k];
+            L[i * m + j] = t / d;
+        }
+    }
+    return 0;
+}
+
+/* L y = b, then L^T x = y */
+static void dense_cholesky_solve(int64_t m, const double *L, const double *b, double *x) {
+    for (int64_t i = 0; i < m; ++i) {
+        double t = b[i];
+        for (int64_t k = 0; k < i; ++k) t -= L[i * m + k] * x[k];
+        x[i] = t / L[i * m + i];
+    }
+    for (int64_t i = m - 1; i >= 0; --i) {
+        double t = x[i];
+        for (int64_t k = i + 1; k < m; ++k) t -= L[k * m + i] * x[k];
+        x[i] = t / L[i * m + i];
+    }
 }
 
 int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
@@ -609,32 +659,83 @@ int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const do
     double *L = (double *)calloc((size_t)(n * n), sizeof(double));
     for (int64_t i = 0; i < n; ++i)
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) L[i * n + ci[k]] = v[k];
-    /* A = L L^T, lower triangle overwritten (textbook column-by-column form) */
-    for (int64_t j = 0; j < n; ++j) {
-        double d = L[j * n + j];
-        for (int64_t k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
-        if (!(d > 0.0)) { free(L); return 1; }
-        d = sqrt(d);
-        L[j * n + j] = d;
-        for (int64_t i = j + 1; i < n; ++i) {
-            double t = L[i * n + j];
-            for (int64_t k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
-            L[i * n + j] = t / d;
-        }
-    }
-    /* L y = b, then L^T x = y */
-    for (int64_t i = 0; i < n; ++i) {
-        double t = b[i];
-        for (int64_t k = 0; k < i; ++k) t -= L[i * n + k] * x[k];
-        x[i] = t / L[i * n + i];
-    }
-    for (int64_t i = n - 1; i >= 0; --i) {
-        double t = x[i];
-        for (int64_t k = i + 1; k < n; ++k) t -= L[k * n + i] * x[k];
-        x[i] = t / L[i * n + i];
-    }
+    if (dense_cholesky(n, L)) { free(L); return 1; }
+    dense_cholesky_solve(n, L, b, x);
     free(L);
     return 0;
+}
+
+/* ------------------------------------------------------- Block-Jacobi -- */
+/* The block-Jacobi preconditioner named among the paper's preconditioners
+ * (Sec. 3.1, with BiCGSTAB; Sec. 4.1, Fig. 5): M = blockdiag(A_11, ..., A_mm),
+ * A_jj the diagonal block of the rows [j bs, min(n, (j+1) bs)) -- bs
+ * consecutive unknowns, the last block possibly shorter.  W holds each
+ * block's inverse, dense row-major, nblk x bs x bs; a short last block fills
+ * its leading m x m corner and leaves the rest 0.  Column c of A_jj^{-1} is
+ * the Cholesky solution of A_jj w = e_c.  Returns 0, or 1 if a block is not
+ * SPD. */
+int orc_bjacobi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+                double *W) {
+    if (bs < 1) return 1;
+    const int64_t nblk = (n + bs - 1) / bs;
+    double *L = (double *)malloc(sizeof(double) * bs * bs);
+    double *e = (double *)malloc(sizeof(double) * bs);
+    double *w = (double *)malloc(sizeof(double) * bs);
+    int rc = 0;
+    for (int64_t j = 0; j < nblk && !rc; ++j) {
+        const int64_t s = j * bs;
+        const int64_t m = (n - s < bs) ? n - s : bs;
+        for (int64_t a = 0; a < m * m; ++a) L[a] = 0.0;
+        for (int64_t a = 0; a < m; ++a)
+            for (int64_t k = rp[s + a]; k < rp[s + a + 1]; ++k)
+                if (ci[k] >= s && ci[k] < s + m) L[a * m + (ci[k] - s)] = v[k];
+        double *Wj = W + j * bs * bs;
+        for (int64_t a = 0; a < (int64_t)bs * bs; ++a) Wj[a] = 0.0;
+        if (dense_cholesky(m, L)) { rc = 1; break; }
+        for (int64_t c = 0; c < m; ++c) {
+            for (int64_t a = 0; a < m; ++a) e[a] = (a == c) ? 1.0 : 0.0;
+            dense_cholesky_solve(m, L, e, w);
+            for (int64_t a = 0; a < m; ++a) Wj[a * bs + c] = w[a];
+        }
+    }
+    free(L); free(e); free(w);
+    return rc;
+}
+
+/* z = M^{-1} r: z_B = W_j r_B for every block */
+void orc_bjacobi_apply(int64_t n, int bs, const double *W, const double *r, double *z) {
+    const int64_t nblk = (n + bs - 1) / bs;
+    for (int64_t j = 0; j < nblk; ++j) {
+        const int64_t s = j * bs;
+        const int64_t m = (n - s < bs) ? n - s : bs;
+        const double *Wj = W + j * bs * bs;
+        for (int64_t a = 0; a < m; ++a) {
+            double t = 0.0;
+            for (int64_t c = 0; c < m; ++c) t += Wj[a * bs + c] * r[s + c];
+            z[s + a] = t;
+        }
+    }
+}
+
+struct bj_ctx { int bs; const double *W; };
+static void bjacobi_apply_cb(int64_t n, const void *ctx, const double *r, double *z) {
+    const struct bj_ctx *c = (const struct bj_ctx *)ctx;
+    orc_bjacobi_apply(n, c->bs, c->W, r, z);
+}
+
+int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+               const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
+               double *relres) {
+    *iters = 0;
+    *relres = 0.0;
+    if (bs < 1) return 2;
+    const int64_t nblk = (n + bs - 1) / bs;
+    double *W = (double *)malloc(sizeof(double) * (nblk > 0 ? nblk : 1) * bs * bs);
+    if (orc_bjacobi(n, rp, ci, v, bs, W)) { free(W); return 2; }
+    struct bj_ctx c = {bs, W};
+    const int st = pcg_core(n, rp, ci, v, bjacobi_apply_cb, &c, b, x, tol, maxit, iters, relres);
+    free(W);
+    return st;
 }
 
 /* ----------------------------------------------------------- SELL-C-sigma -- */

@@ -81,6 +81,19 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
             const double *b, double *x, double tol, int64_t maxit,
             int64_t *iters, double *relres);
 
+/* Block-Jacobi (Sec. 3.1, Sec. 4.1): M = blockdiag of the diagonal blocks of
+ * bs consecutive rows (the last one shorter when bs does not divide n).
+ * orc_bjacobi writes each block's inverse, dense row-major, into W
+ * (ceil(n/bs) x bs x bs; a short block fills its leading corner, the rest 0);
+ * returns 0, or 1 if a block is not SPD.  orc_bjacobi_apply: z = M^{-1} r.
+ * orc_pcg_bj: orc_pcg with this M (returns 2 if a block is not SPD). */
+int orc_bjacobi(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+                double *W);
+void orc_bjacobi_apply(int64_t n, int bs, const double *W, const double *r, double *z);
+int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+               const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
+               double *relres);
+
 /* Dense Cholesky solve A x = b (n small).  Returns 0, or 1 if A is not SPD. */
 int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                        const double *b, double *x);
