@@ -196,6 +196,38 @@ int sell_autotune(const gb_fem_system *sys, const double *d_b, int precision, in
  * another value. */
 int sell_set_variant(gb_sell *A, int variant);
 
+/* Block-Jacobi preconditioner (the paper's Block-Jacobi, Sec. 3.1 and Sec.
+ * 4.1): M = blockdiag(K_11, ..., K_mm), K_jj the diagonal block of the bs
+ * consecutive free dofs [j bs, min(n, (j+1) bs)) in the original (free-dof)
+ * order; the last block is shorter when bs does not divide n.
+ * sell_block_jacobi computes each block's inverse on the device (Gauss-Jordan
+ * elimination in fp64, symmetrised) and attaches it to A, replacing any
+ * earlier one; bs = 0 detaches it.  bs in {0, 1, 2, 4, 8, 16, 32}, and A's
+ * sigma must divide 256: then the rows of a block share one 256-row window of
+ * the SELL permutation, which the fused PCG update works on.  Synchronises
+ * `stream` (also before freeing earlier blocks).  Errors: GB_EINVAL (bs or
+ * sigma), GB_ENOMEM, GB_BREAKDOWN (a block is not positive definite).  A
+ * solve uses it with PcgOptions.precond = GB_PC_BLOCK_JACOBI.
+ * sell_block_jacobi_info: the attached data (device pointers, owned by A):
+ * d_w holds per block the upper triangle of its inverse, row-major (bs(bs+1)/2
+ * doubles per block, rows and columns past a short block's end 0), d_w32 the
+ * same in fp32, d_loc per free dof o the SELL position of o minus
+ * 256 floor(o/256) (nblk * bs bytes); lam_bound = max absolute row sum of the
+ * inverses (>= the largest eigenvalue of M^-1).  bs = 0 when none is attached.
+ * sell_block_jacobi_apply: y = M^-1 x (n doubles each, free-dof order);
+ * GB_EINVAL without attached blocks; synchronises `stream`. */
+typedef struct gb_bjacobi_info {
+    int32_t bs, reserved;
+    int64_t nblk;
+    const double *d_w;
+    const float *d_w32;
+    const uint8_t *d_loc;
+    double lam_bound;
+} gb_bjacobi_info;
+int sell_block_jacobi(gb_sell *A, int bs, void *stream);
+int sell_block_jacobi_info(const gb_sell *A, gb_bjacobi_info *out);
+int sell_block_jacobi_apply(const gb_sell *A, const double *d_x, double *d_y, void *stream);
+
 /* ------------------------------------------------------------------ PCG --
  * Jacobi-PCG: r = b - A x0, z = D^{-1} r, p = z; iterate q = A p,
  * alpha = r.z / p.q, x += alpha p, r -= alpha q, z = D^{-1} r, beta = r.z'/r.z,
@@ -213,8 +245,13 @@ int sell_set_variant(gb_sell *A, int variant);
  * instead of restarts -- one fp32 recurrence keeps its search direction; each
  * time its residual has dropped tenfold, x += d and r = b - A x are formed in
  * fp64, the test is made in fp64 and the fp32 residual is replaced by the
- * true one (stats.outer counts these updates).  pcg_solve only. */
+ * true one (stats.outer counts these updates).  pcg_solve only.
+ * precond GB_PC_BLOCK_JACOBI replaces D^{-1} by the block inverses attached
+ * with sell_block_jacobi (pcg_solve with GB_F64, GB_F32_IR or GB_BF16_IR --
+ * the inner solve then applies the fp32 copy; GB_EINVAL otherwise, and in
+ * pcg_solve_batched and pcg_solve_noalloc). */
 enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2, GB_F32_RU = 3, GB_BF16_RU = 4 };
+enum { GB_PC_JACOBI = 0, GB_PC_BLOCK_JACOBI = 1 };
 
 typedef struct PcgOptions {
     double tol;            /* Eq. (2) threshold, e.g. 1e-10 */
@@ -231,6 +268,7 @@ typedef struct PcgOptions {
     int32_t persist_off;   /* pcg_solve_batched: 0 (default) = systems with n * k2 <= 32768 (k2: the
                               power of two >= k) are solved whole by one CTA each in a single
                               persistent launch; 1 = every system in the multi-launch loop */
+    int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
 } PcgOptions;
 
 typedef struct PcgStats {
@@ -351,7 +389,10 @@ int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const Pc
  * milliseconds of each of the iteration's three kernels to h_ms[0] (SpMV +
  * p.Ap), h_ms[1] (x, r update + r.z, r.r) and h_ms[2] (p update).  The
  * iterations run even past convergence (the scalars are reset each time), so
- * every timed launch does a full pass.  Synchronises `stream`. */
+ * every timed launch does a full pass.  precision | GB_KT_BLOCK_JACOBI times
+ * the block-Jacobi iteration instead (h_ms[1]: the x, r update with z = M^-1 r;
+ * GB_EINVAL without sell_block_jacobi data).  Synchronises `stream`. */
+enum { GB_KT_BLOCK_JACOBI = 256 };
 int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int iters, void *stream,
                      double *h_ms);
 

@@ -23,16 +23,16 @@ class _DevArray:
 
 def _view(ptr, shape, dtype):
     typestr = {torch.int32: "<i4", torch.int64: "<i8", torch.float64: "<f8",
-               torch.float32: "<f4", torch.int16: "<i2"}[dtype]
+               torch.float32: "<f4", torch.int16: "<i2", torch.uint8: "|u1"}[dtype]
     if int(ptr or 0) == 0 or any(s == 0 for s in shape):
         return torch.empty(shape, dtype=dtype, device="cuda")
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
 
 
 def _opts(tol=1e-10, max_iter=0, precision=G.GB_F64, max_outer=0, inner_tol=0.0, check_every=0,
-          use_graph=1, x0_zero=1, spmv_variant=0, persist_off=0):
+          use_graph=1, x0_zero=1, spmv_variant=0, persist_off=0, precond=G.GB_PC_JACOBI):
     return G.PcgOptions(tol, max_iter, precision, max_outer, inner_tol, check_every, use_graph,
-                        x0_zero, spmv_variant, persist_off)
+                        x0_zero, spmv_variant, persist_off, precond)
 
 
 class FemSystem:
@@ -190,6 +190,35 @@ class Sell:
         y = torch.empty_like(x)
         G.check(G.lib().sell_spmv(self.handle, G.ptr(x.contiguous()), G.ptr(y), G.stream_ptr(self._stream)),
                 "sell_spmv")
+        return y
+
+    def block_jacobi(self, bs, stream=None):
+        """sell_block_jacobi: attaches the block-Jacobi inverses (bs = 0 detaches them)."""
+        G.check(G.lib().sell_block_jacobi(self.handle, int(bs),
+                                          G.stream_ptr(stream if stream is not None else self._stream)),
+                "sell_block_jacobi")
+        return self
+
+    def block_jacobi_info(self):
+        """The attached block-Jacobi data: bs, nblk, lam_bound and copies of the packed
+        inverses (nblk, bs(bs+1)/2) in fp64 and fp32 and the row positions (nblk*bs)."""
+        i = G.gb_bjacobi_info()
+        G.check(G.lib().sell_block_jacobi_info(self.handle, C.byref(i)), "sell_block_jacobi_info")
+        if i.bs == 0:
+            return {"bs": 0}
+        T = i.bs * (i.bs + 1) // 2
+        return {"bs": i.bs, "nblk": i.nblk, "lam_bound": i.lam_bound,
+                "w": _view(i.d_w, (i.nblk, T), torch.float64).clone(),
+                "w32": _view(i.d_w32, (i.nblk, T), torch.float32).clone(),
+                "loc": _view(i.d_loc, (i.nblk * i.bs,), torch.uint8).clone()}
+
+    def block_jacobi_apply(self, x, stream=None):
+        """sell_block_jacobi_apply: y = M^-1 x (free-dof order)."""
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        G.check(G.lib().sell_block_jacobi_apply(self.handle, G.ptr(x), G.ptr(y),
+                                                G.stream_ptr(stream if stream is not None else self._stream)),
+                "sell_block_jacobi_apply")
         return y
 
     def kernel_times(self, b, precision=G.GB_F64, iters=50, stream=None):

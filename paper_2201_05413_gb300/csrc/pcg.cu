@@ -19,6 +19,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bjacobi.cuh"
 #include "pcg.cuh"
 #include "spmv_tma.cuh"
 
@@ -225,15 +226,6 @@ __global__ void __launch_bounds__(NT) k_spmv_pq(SellView A, const TV *__restrict
 #endif
 constexpr int UPD_U = GB_UPD_U;
 
-// ||r||^2 is needed only when it can meet the Eq. (2) threshold: since
-// r.D^-1 r <= max(D^-1) ||r||^2, while rho = r.z stays above max(D^-1) times
-// the threshold (S->dmax > 0: max(D^-1) of the matrix) the x/r update skips
-// the r.r sums; when this iteration's r.z falls below that bound with r.r
-// skipped, the p update computes r.r from the r it reads anyway and makes the
-// test there, in the same iteration -- the stopping iteration is unchanged.
-__device__ __forceinline__ bool want_rr(const PcgScal *S) {
-    return !(S->dmax > 0.0) || S->rho <= S->dmax * S->thresh;
-}
 
 // x += alpha p, r -= alpha q, r.D^-1 r (and r.r, see want_rr); z = D^-1 r is
 // stored when z is given (the p update then reads it instead of D^-1 and r).
@@ -557,14 +549,18 @@ static Grids pick_grids(int64_t n, int C) {
 template <class TV, class TX, class TD>
 static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
                               TX *q, TX *z, double *partials, PcgScal *S, const Grids &g, cudaStream_t st,
-                              int variant = 0) {
+                              int variant = 0, const BjView *bj = nullptr) {
     if (variant == 0 && A.C == 32 && A.warp_chunk) launch_spmv_tma<TV, TX>(A, val, p, q, partials, S, st);
     else switch (A.C) {
     case 32: ::gb::count_launches(1); k_spmv_pq<TV, TX, 32><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     case 64: ::gb::count_launches(1); k_spmv_pq<TV, TX, 64><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     default: ::gb::count_launches(1); k_spmv_pq<TV, TX, 128><<<g.spmv, NT, 0, st>>>(A, val, p, q, partials, S); break;
     }
-    ::gb::count_launches(1); k_update<TX, TD><<<g.upd, NT, 0, st>>>(A.n, x, r, p, q, dinv, z, partials, S);
+    if (bj && bj->bs) {  // block-Jacobi: z = M^-1 r in the x/r update (z always stored)
+        launch_update_bj<TX, TX>(*bj, A.n, x, r, p, q, z, partials, S, st);
+    } else {
+        ::gb::count_launches(1); k_update<TX, TD><<<g.upd, NT, 0, st>>>(A.n, x, r, p, q, dinv, z, partials, S);
+    }
     ::gb::count_launches(1); k_pupdate<TX, TD><<<g.upd, NT, 0, st>>>(A.n, p, r, dinv, z, partials, S);
 }
 
@@ -648,7 +644,7 @@ static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &
 
 // partial-sum slots every solver kernel may write (2 per block of the largest grid)
 static size_t partial_slots(const gb_sell *A, const Grids &g) {
-    int blocks = std::max(g.spmv, g.vec);
+    int blocks = std::max(std::max(g.spmv, g.vec), bj_grid(A->n));
     if (A->warp_chunk) blocks = std::max(blocks, std::max(A->nwarps, A->nwarps5) / TMA_WARPS);
     return 3 * (size_t)blocks;
 }
@@ -695,9 +691,11 @@ struct Work {
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *b = nullptr, *partials = nullptr;
     double *z = nullptr;  // fp64 D^-1 r, when the workspace has room for it
     float *r32 = nullptr, *d32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    float *z32 = nullptr;  // fp32 M^-1 r (block-Jacobi inner solves)
     PcgScal *S = nullptr, *S2 = nullptr;
     ~Work() {
         mem.release(x); mem.release(r); mem.release(p); mem.release(q); mem.release(b); mem.release(z);
+        mem.release(z32);
         mem.release(partials);
         mem.release(r32); mem.release(d32); mem.release(p32); mem.release(q32);
         mem.release(S); mem.release(S2);
@@ -729,15 +727,23 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
     int64_t restarts = 0;
     int status = ST_RUN;
     double rel = std::sqrt(h.rr / h.bb);
-    // max(D^-1): the update defers its r.r sums while they cannot meet Eq. (2)
-    GB_CHECK_CUDA(cudaMemcpyAsync(&w.S->dmax, &A->dinv_max, sizeof(double), cudaMemcpyHostToDevice, st));
+    // bound of lmax(M^-1): the update defers its r.r sums while they cannot meet Eq. (2)
+    const bool use_bj = o.precond == GB_PC_BLOCK_JACOBI;
+    const BjView bj = A->bj_view();
+    GB_CHECK_CUDA(cudaMemcpyAsync(&w.S->dmax, use_bj ? &A->bj_lam : &A->dinv_max, sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
     while (rel > o.tol) {
-        ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
+        if (use_bj) {
+            launch_start_bj<double, double>(bj, n, w.r, w.p, w.partials, w.S, st);
+        } else {
+            ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
+        }
         ++launches;
         GB_CHECK_CUDA(cudaGetLastError());
         auto body = [&](cudaStream_t s) {
             enqueue_iteration<double, double, double>(V, A->val, A->dinv, w.x, w.r, w.p, w.q, w.z, w.partials, w.S, g, s,
-                                                      o.spmv_variant ? o.spmv_variant : A->variant_hint);
+                                                      o.spmv_variant ? o.spmv_variant : A->variant_hint,
+                                                      use_bj ? &bj : nullptr);
         };
         GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr));
         GB_TRY(read_scal(w.S, &h, st));
@@ -756,7 +762,9 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
     stats->relres = rel;
     stats->status = map_status(status);
     stats->kernel_launches = launches + 3 * h.it;
-    const double bytes_iter = (double)A->nnz * 12.0 + 7.0 * n * 8.0;
+    // block-Jacobi: the packed inverses and row positions replace D^-1
+    const double bytes_iter = (double)A->nnz * 12.0 + 7.0 * n * 8.0 +
+                              (use_bj ? (double)A->bj_nblk * (A->bj_bs * (A->bj_bs + 1) / 2 * 8.0 + A->bj_bs) - 8.0 * n : 0.0);
     stats->bytes_moved = bytes_iter * (double)h.it;
     return GB_OK;
 }
@@ -774,6 +782,9 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
     GB_TRY(mem.alloc_n(&w.p32, n));
     GB_TRY(mem.alloc_n(&w.q32, n));
     GB_TRY(mem.alloc_n(&w.S2, 1));
+    const bool use_bj = o.precond == GB_PC_BLOCK_JACOBI;
+    const BjView bj = A->bj_view();
+    if (use_bj) GB_TRY(mem.alloc_n(&w.z32, n));
     enqueue_residual(V, o.x0_zero ? nullptr : w.x, w.b, w.r, w.partials, w.S, 1, o.tol, g, st);
     ++launches;
     PcgScal h{};
@@ -806,18 +817,24 @@ static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
             hs.thresh = o.inner_tol * o.inner_tol;
             GB_CHECK_CUDA(cudaMemcpyAsync(w.S2, &hs, sizeof(PcgScal), cudaMemcpyHostToDevice, st));
         }
-        ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
+        if (use_bj) {
+            launch_start_bj<float, float>(bj, n, w.r32, w.p32, w.partials, w.S2, st);
+        } else {
+            ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S2);
+        }
         launches += 2;
         auto body = [&](cudaStream_t s) {
-            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, (float *)nullptr, w.partials, w.S2, g, s,
-                                                o.spmv_variant ? o.spmv_variant : A->variant_hint);
+            enqueue_iteration<TV, float, float>(V, val_in, A->dinv32, w.d32, w.r32, w.p32, w.q32, w.z32, w.partials, w.S2, g, s,
+                                                o.spmv_variant ? o.spmv_variant : A->variant_hint,
+                                                use_bj ? &bj : nullptr);
         };
         GB_TRY(run_loop(st, w.S2, o.use_graph != 0, o.check_every, body, nullptr));
         PcgScal hi{};
         GB_TRY(read_scal(w.S2, &hi, st));
         inner_total += hi.it;
         launches += 3 * hi.it;
-        bytes += hi.it * ((double)A->nnz * (sval + 4.0) + 7.0 * n * 4.0);
+        bytes += hi.it * ((double)A->nnz * (sval + 4.0) + 7.0 * n * 4.0 +
+                          (use_bj ? (double)A->bj_nblk * (A->bj_bs * (A->bj_bs + 1) / 2 * 4.0 + A->bj_bs) - 4.0 * n : 0.0));
         // x += ||r|| d ; r = b - A x in fp64
         ::gb::count_launches(1); k_correct<<<g.vec, NT, 0, st>>>(n, w.x, rn, w.d32);
         enqueue_residual(V, w.x, w.b, w.r, w.partials, w.S, 0, o.tol, g, st);
@@ -962,6 +979,13 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
                "pcg_solve: fp32-inner precisions need fp32 values (val_types)");
     GB_REQUIRE((o.precision != GB_BF16_IR && o.precision != GB_BF16_RU) || A->val16,
                "pcg_solve: bf16-inner precisions need bf16 values (val_types)");
+    GB_REQUIRE(o.precond == GB_PC_JACOBI || o.precond == GB_PC_BLOCK_JACOBI, "pcg_solve: bad precond %d",
+               o.precond);
+    GB_REQUIRE(o.precond != GB_PC_BLOCK_JACOBI || A->bj_bs > 0,
+               "pcg_solve: GB_PC_BLOCK_JACOBI without block-Jacobi data (sell_block_jacobi)");
+    GB_REQUIRE(o.precond != GB_PC_BLOCK_JACOBI || o.precision == GB_F64 || o.precision == GB_F32_IR ||
+                   o.precision == GB_BF16_IR,
+               "pcg_solve: GB_PC_BLOCK_JACOBI with GB_F64, GB_F32_IR or GB_BF16_IR only");
     cudaStream_t st = (cudaStream_t)stream;
     Work w;
     w.mem = Mem(nullptr, st);
@@ -1030,6 +1054,9 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                              void *stream, double *h_ms) {
     GB_REQUIRE(A && d_b && h_ms, "pcg_kernel_times: NULL argument");
     GB_REQUIRE(iters >= 1 && iters <= 100000, "pcg_kernel_times: iters must be in 1..100000");
+    const bool use_bj = (precision & GB_KT_BLOCK_JACOBI) != 0;
+    precision &= ~GB_KT_BLOCK_JACOBI;
+    GB_REQUIRE(!use_bj || A->bj_bs > 0, "pcg_kernel_times: GB_KT_BLOCK_JACOBI without block-Jacobi data");
     GB_REQUIRE(precision >= GB_F64 && precision <= GB_BF16_IR, "pcg_kernel_times: bad precision");
     GB_REQUIRE(precision != GB_F32_IR || A->val32, "pcg_kernel_times: no fp32 values");
     GB_REQUIRE(precision != GB_BF16_IR || A->val16, "pcg_kernel_times: no bf16 values");
@@ -1049,22 +1076,26 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
     GB_TRY(w.mem.alloc_n(&w.d32, n));
     GB_TRY(w.mem.alloc_n(&w.p32, n));
     GB_TRY(w.mem.alloc_n(&w.q32, n));
+    GB_TRY(w.mem.alloc_n(&w.z32, n));
     GB_TRY(w.mem.alloc_n(&w.partials, partial_slots(A, g)));
     GB_TRY(w.mem.alloc_n(&w.S, 1));
+    const BjView bj = A->bj_view();
     PcgScal hs{};
     hs.maxit = (long long)iters + 1;
     hs.thresh = -1.0;  // never converges: every timed launch is a full pass
     // fp64: the solver's launch sequence (z stored, r.r sums deferred)
-    if (precision == GB_F64) hs.dmax = A->dinv_max;
+    if (precision == GB_F64) hs.dmax = use_bj ? A->bj_lam : A->dinv_max;
     GB_CHECK_CUDA(cudaMemcpyAsync(w.S, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
     GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
     enqueue_residual(V, nullptr, w.b, w.r, w.partials, w.S, 0, 0.0, g, st);
     if (precision == GB_F64) {
-        ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S);
+        if (use_bj) launch_start_bj<double, double>(bj, n, w.r, w.p, w.partials, w.S, st);
+        else { ::gb::count_launches(1); k_start<double, double><<<g.vec, NT, 0, st>>>(n, w.r, A->dinv, w.p, w.partials, w.S); }
     } else {
         ::gb::count_launches(1); k_scale_down<<<g.vec, NT, 0, st>>>(n, w.r, 1.0, w.r32, w.d32);
-        ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S);
+        if (use_bj) launch_start_bj<float, float>(bj, n, w.r32, w.p32, w.partials, w.S, st);
+        else { ::gb::count_launches(1); k_start<float, float><<<g.vec, NT, 0, st>>>(n, w.r32, A->dinv32, w.p32, w.partials, w.S); }
     }
     GB_CHECK_CUDA(cudaGetLastError());
     std::vector<cudaEvent_t> ev(3 * (size_t)iters + 1);
@@ -1085,7 +1116,8 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                     default: ::gb::count_launches(1); k_spmv_pq<double, double, 128><<<g.spmv, NT, 0, st>>>(V, A->val, w.p, w.q, w.partials, w.S); break;
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<double, double><<<g.upd, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.z, w.partials, w.S);
+                    if (use_bj) launch_update_bj<double, double>(bj, n, w.x, w.r, w.p, w.q, w.z, w.partials, w.S, st);
+                    else { ::gb::count_launches(1); k_update<double, double><<<g.upd, NT, 0, st>>>(n, w.x, w.r, w.p, w.q, A->dinv, w.z, w.partials, w.S); }
                 } else {
                     ::gb::count_launches(1); k_pupdate<double, double><<<g.upd, NT, 0, st>>>(n, w.p, w.r, A->dinv, w.z, w.partials, w.S);
                 }
@@ -1105,9 +1137,10 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
                         }
                     }
                 } else if (k == 1) {
-                    ::gb::count_launches(1); k_update<float, float><<<g.upd, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, (float *)nullptr, w.partials, w.S);
+                    if (use_bj) launch_update_bj<float, float>(bj, n, w.d32, w.r32, w.p32, w.q32, w.z32, w.partials, w.S, st);
+                    else { ::gb::count_launches(1); k_update<float, float><<<g.upd, NT, 0, st>>>(n, w.d32, w.r32, w.p32, w.q32, A->dinv32, (float *)nullptr, w.partials, w.S); }
                 } else {
-                    ::gb::count_launches(1); k_pupdate<float, float><<<g.upd, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, (const float *)nullptr, w.partials, w.S);
+                    ::gb::count_launches(1); k_pupdate<float, float><<<g.upd, NT, 0, st>>>(n, w.p32, w.r32, A->dinv32, use_bj ? w.z32 : (const float *)nullptr, w.partials, w.S);
                 }
             }
             cudaEventRecord(ev[3 * (size_t)i + k + 1], st);
@@ -1289,6 +1322,7 @@ extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_
     *stats = PcgStats{};
     PcgOptions o = defaults(opt, A->n);
     GB_REQUIRE(o.precision == GB_F64, "pcg_solve_noalloc: only precision GB_F64 is available");
+    GB_REQUIRE(o.precond == GB_PC_JACOBI, "pcg_solve_noalloc: the Jacobi preconditioner only");
     o.use_graph = 0;  // graph objects would allocate: the loop is polled direct launches
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);

@@ -19,7 +19,7 @@ struct PcgScal {
     double bb;      // ||b||^2
     double thresh;  // tol^2 ||b||^2
     double pz;      // reliable update: coefficient of z in the restored p
-    double dmax;    // max(D^-1) for the deferred r.r test (0: r.r every iteration)
+    double dmax;    // bound of lmax(M^-1) for the deferred r.r test (0: r.r every iteration)
     long long it, maxit;
     int done, status;
     unsigned int ticket;  // last-block counter
@@ -84,6 +84,17 @@ __device__ __forceinline__ void st_pack(T *p, int64_t i, const T (&o)[N]) {
 #pragma unroll
     for (int k = 0; k < N; ++k) v.v[k] = o[k];
     reinterpret_cast<Pack<T, N> *>(p)[i] = v;
+}
+
+// ||r||^2 is needed only when it can meet the Eq. (2) threshold: since
+// r.M^-1 r <= lmax(M^-1) ||r||^2, while rho = r.z stays above an upper bound of
+// lmax(M^-1) times the threshold (S->dmax > 0: max(D^-1) for Jacobi, the
+// largest absolute row sum of the inverses for block-Jacobi) the x/r update skips
+// the r.r sums; when this iteration's r.z falls below that bound with r.r
+// skipped, the p update computes r.r from the r it reads anyway and makes the
+// test there, in the same iteration -- the stopping iteration is unchanged.
+__device__ __forceinline__ bool want_rr(const PcgScal *S) {
+    return !(S->dmax > 0.0) || S->rho <= S->dmax * S->thresh;
 }
 
 __device__ __forceinline__ void stop(PcgScal *S, int status) {

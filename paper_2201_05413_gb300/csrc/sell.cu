@@ -392,5 +392,6 @@ extern "C" void sell_destroy(gb_sell *A) {
     m.release(A->dinv); m.release(A->dinv32);
     m.release(A->chunk_w); m.release(A->chunk_ptr); m.release(A->warp_chunk); m.release(A->warp_chunk5);
     m.release(A->col); m.release(A->col16); m.release(A->val); m.release(A->val32); m.release(A->val16);
+    m.release(A->bj_w); m.release(A->bj_w32); m.release(A->bj_loc);
     delete A;
 }

@@ -26,6 +26,16 @@ struct SellView {
     int nwarps5;
 };
 
+// Block-Jacobi data of a matrix (bjacobi.cuh), passed by value to kernels.
+struct BjView {
+    int bs = 0;                    // 0: no block-Jacobi data
+    int64_t nblk = 0;
+    const double *w = nullptr;     // nblk x bs(bs+1)/2: upper triangle of each inverse, row-major
+    const float *w32 = nullptr;    // the same in fp32
+    const uint8_t *loc = nullptr;  // nblk*bs: SELL position of free dof o minus 256 floor(o/256)
+    double lam = 0.0;              // upper bound of the largest eigenvalue of M^-1 (row sums)
+};
+
 }  // namespace gb
 
 struct gb_sell {
@@ -36,6 +46,13 @@ struct gb_sell {
     int16_t *col16 = nullptr;
     int nwarps = 0, nwarps5 = 0;
     int variant_hint = 0;  // SpMV variant solves use by default (set by sell_autotune)
+    // block-Jacobi preconditioner (sell_block_jacobi): packed inverses, row positions
+    int bj_bs = 0;
+    int64_t bj_nblk = 0;
+    double *bj_w = nullptr;
+    float *bj_w32 = nullptr;
+    uint8_t *bj_loc = nullptr;
+    double bj_lam = 0.0;
     double dinv_max = 0.0; // max_i 1/K_ii (host copy)
     int64_t *chunk_ptr = nullptr;
     double *val = nullptr, *dinv = nullptr;
@@ -45,5 +62,10 @@ struct gb_sell {
     gb::SellView view() const {
         return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32,
                             chunk_w, warp_chunk, nwarps, col16, warp_chunk5, nwarps5};
+    }
+    gb::BjView bj_view() const {
+        gb::BjView b;
+        b.bs = bj_bs; b.nblk = bj_nblk; b.w = bj_w; b.w32 = bj_w32; b.loc = bj_loc; b.lam = bj_lam;
+        return b;
     }
 };

@@ -18,6 +18,8 @@ GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA = 0, -1, -2, -3
 GB_NOT_CONVERGED, GB_BREAKDOWN, GB_TIMEOUT, GB_TOO_LARGE, GB_PENDING = -4, -5, -6, -7, 1
 GB_VAL_F64, GB_VAL_F32, GB_VAL_BF16, GB_IDX16 = 1, 2, 4, 8
 GB_F64, GB_F32_IR, GB_BF16_IR, GB_F32_RU, GB_BF16_RU = 0, 1, 2, 3, 4
+GB_PC_JACOBI, GB_PC_BLOCK_JACOBI = 0, 1
+GB_KT_BLOCK_JACOBI = 256
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "NOT_CONVERGED",
                 -5: "BREAKDOWN", -6: "TIMEOUT", -7: "TOO_LARGE", 1: "PENDING"}
 
@@ -62,7 +64,7 @@ class PcgOptions(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("spmv_variant", C.c_int32),
-                ("persist_off", C.c_int32)]
+                ("persist_off", C.c_int32), ("precond", C.c_int32)]
 
 
 class PcgStats(C.Structure):
@@ -73,6 +75,11 @@ class PcgStats(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class gb_bjacobi_info(C.Structure):
+    _fields_ = [("bs", C.c_int32), ("reserved", C.c_int32), ("nblk", C.c_int64), ("d_w", C.c_void_p),
+                ("d_w32", C.c_void_p), ("d_loc", C.c_void_p), ("lam_bound", C.c_double)]
 
 
 class SellTuneResult(C.Structure):
@@ -134,6 +141,9 @@ _SIGS = {
                                 C.POINTER(SellTuneResult), C.POINTER(_P)]),
     "sell_set_variant": (C.c_int, [_P, C.c_int]),
     "sell_spmv": (C.c_int, [_P, _P, _P, _P]),
+    "sell_block_jacobi": (C.c_int, [_P, C.c_int, _P]),
+    "sell_block_jacobi_info": (C.c_int, [_P, C.POINTER(gb_bjacobi_info)]),
+    "sell_block_jacobi_apply": (C.c_int, [_P, _P, _P, _P]),
     "sell_destroy": (None, [_P]),
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
