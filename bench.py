@@ -12,7 +12,7 @@ dominant kernel, a seeded serving mix through the continuous-batching server,
 and the CPU oracle timed on this host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --profile-kernels p2 --profile-precision f64   (ncu driver)
+  python bench.py --profile-kernels p2 --profile-precision f64 [--profile-bj 4]   (ncu driver)
 
 N>1 runs as torchrun ranks, one GPU each: independent replicas of the same
 workload (the path has no exchange step), max-over-ranks timing.
@@ -46,6 +46,8 @@ ITERS_FULL = [3597, 8534]
 # launch, `--profile-kernels p2`); None whenever the kernel changes until it is
 # captured again
 NCU_TRAFFIC = {"k_spmv_tma2<double,double>": 640554496, "k_spmv_tma2<float,float>": 423162112}
+# block-Jacobi block size per system (the fastest fp64 solve in the --sweep precond runs)
+BJ_BS = {"2D-P1-jittered-1024": 2, "2D-P2-jittered-1024": 4}
 WORKLOAD = "cfg2: 2D unit square 1024x1024 cells, jittered +-h/4, random diagonals (seed 1), P1 + P2, g=x^2-y^2"
 
 
@@ -64,9 +66,12 @@ def parse():
     ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
                     help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--sweep", default=None, choices=["eps", "rhs"],
-                    help="accuracy vs stopping tolerance (eps) or solve time vs number of right-hand sides (rhs)")
+    ap.add_argument("--sweep", default=None, choices=["eps", "rhs", "precond"],
+                    help="accuracy vs stopping tolerance (eps), solve time vs number of right-hand sides (rhs), "
+                         "or Jacobi vs block-Jacobi block sizes (precond)")
     ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--profile-bj", type=int, default=0, metavar="BS",
+                    help="profiling driver: time the block-Jacobi iteration with blocks of BS rows")
     return ap.parse_args()
 
 
@@ -150,7 +155,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
-    def step(precision=P.GB_F64, host_io=None, collect=None):
+    def step(precision=P.GB_F64, host_io=None, collect=None, bj=None):
         for idx, (name, dim, deg, cells, jit, dm, seed) in enumerate(SYSTEMS):
             d = P.FemSystem(dim, deg, cells, jit, dm, seed)
             A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32)
@@ -159,7 +164,11 @@ def run_ours(args, rank, world):
             else:
                 gB = d.dirichlet(GID)
             b = d.lift(gB)[:, 0]
-            x, st = A.solve(b, tol=TOL, max_iter=400000, precision=precision)
+            kw = {}
+            if bj:  # block-Jacobi: setup of the block inverses inside the step
+                A.block_jacobi(bj[name])
+                kw["precond"] = P.GB_PC_BLOCK_JACOBI
+            x, st = A.solve(b, tol=TOL, max_iter=400000, precision=precision, **kw)
             if host_io is not None:
                 host_io["x"][idx].copy_(x, non_blocking=True)
             if collect is not None:
@@ -213,6 +222,12 @@ def run_ours(args, rank, world):
     tmx = timed(args.steps, precision=P.GB_F32_RU)
     mixed_value = len(SYSTEMS) * args.steps / sum(tmx)
 
+    # ---- block-Jacobi preconditioner (fp64), same workload
+    bj_info = []
+    step(collect=bj_info, bj=BJ_BS)
+    tbj = timed(args.steps, bj=BJ_BS)
+    bj_value = len(SYSTEMS) * args.steps / sum(tbj)
+
     # ---- e2e through the public API with host buffers
     host_io = {"gB": [], "x": []}
     for name, d, A, b, st in info:
@@ -262,6 +277,9 @@ def run_ours(args, rank, world):
         per_sys.append({"system": name, "n": d.n_free, "nnz": d.nnz, "iterations": st["iterations"],
                         "relres": st["relres"], "solve_ms": round(st["solve_ms"], 3),
                         "effective_GBps": round(st["bytes_moved"] / (st["solve_ms"] * 1e-3) / 1e9, 1)})
+    for (name, d, A, b, st), row in zip(bj_info, per_sys):
+        row["f64_block_jacobi"] = {"bs": BJ_BS[name], "iterations": st["iterations"], "relres": st["relres"],
+                                   "solve_ms": round(st["solve_ms"], 3)}
     for (name, d, A, b, st), row in zip(mixed_info, per_sys):
         row["f32_ru"] = {"iterations": st["iterations"], "reliable_updates": st["outer"],
                          "fallback_iterations": st["fallback_iterations"], "relres": st["relres"],
@@ -279,6 +297,9 @@ def run_ours(args, rank, world):
         "mixed_f32_ru": {"value": round(mixed_value, 4), "unit": "solves/s",
                          "dtype": "f32 recurrence (fp32 values/vectors) + f64 reliable updates, test and solution",
                          "speedup_vs_f64": round(mixed_value / value * world, 3)},
+        "block_jacobi_f64": {"value": round(bj_value, 4), "unit": "solves/s", "dtype": "f64",
+                             "bs": BJ_BS, "speedup_vs_f64": round(bj_value / value * world, 3),
+                             "note": "block-Jacobi PCG (Sec. 3.1/4.1), block setup inside the timed step"},
         "per_system": per_sys,
         "kernel_ms": {"f64": {"spmv_pq": ms64[0], "update": ms64[1], "pupdate": ms64[2]},
                       "f32": {"spmv_pq": ms32[0], "update": ms32[1], "pupdate": ms32[2]}},
@@ -385,10 +406,13 @@ def run_profile(args):
     A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32 | P.GB_VAL_BF16)
     b = d.lift(d.dirichlet(gid))[:, 0]
     prec = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR}[args.profile_precision]
+    if args.profile_bj:
+        A.block_jacobi(args.profile_bj)
+        prec |= P.gbpcg.GB_KT_BLOCK_JACOBI
     ms = A.kernel_times(b, prec, args.profile_iters)
     torch.cuda.synchronize()
     print(json.dumps({"system": args.profile_kernels, "precision": args.profile_precision, "n": A.n,
-                      "nnz": A.nnz, "kernel_ms": ms}))
+                      "nnz": A.nnz, "block_jacobi": args.profile_bj, "kernel_ms": ms}))
 
 
 MULTI_SPEC = (2, 2, 2048, 1, 1, 2)  # cfg4: 2D jittered 2048^2 P2, seed 2
@@ -571,6 +595,46 @@ def run_sweep_rhs():
         print(json.dumps(row), flush=True)
 
 
+def run_sweep_precond():
+    """Jacobi against block-Jacobi (blocks of 1..32 consecutive free dofs) on
+    the sweep systems at Eq. (2)'s 1e-10: iterations, solve time (block setup
+    excluded, reported apart), x/r-update kernel time, fp64 and fp32-inner
+    refinement; x_err (Eq. 1) as in the eps sweep."""
+    import torch
+    import paper_2201_05413_gb300 as P
+    P.load()
+    for name, spec, gid, exact in EPS_SYSTEMS:
+        d = P.FemSystem(*spec)
+        A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32)
+        b = d.lift(d.dirichlet(gid))[:, 0]
+        if exact:
+            ref = d.dirichlet(gid, which="free")[:, 0]
+        else:
+            ref, _ = A.solve(b, tol=1e-13, max_iter=2000000, raise_on_fail=False)
+        for bs in (0, 1, 2, 4, 8, 16, 32):
+            row = {"sweep": "precond", "system": name, "n": A.n, "precond": "jacobi" if bs == 0 else "block_jacobi",
+                   "bs": bs}
+            kw, flag = {}, 0
+            if bs:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                A.block_jacobi(bs)
+                row["setup_ms"] = round(1e3 * (time.perf_counter() - t0), 3)
+                kw, flag = {"precond": P.GB_PC_BLOCK_JACOBI}, P.gbpcg.GB_KT_BLOCK_JACOBI
+            for pn, pv in (("f64", P.GB_F64), ("f32_ir", P.GB_F32_IR)):
+                A.solve(b, tol=TOL, max_iter=2000000, precision=pv, raise_on_fail=False, **kw)  # warm
+                x, st = A.solve(b, tol=TOL, max_iter=2000000, precision=pv, raise_on_fail=False, **kw)
+                ms = A.kernel_times(b, pv | flag, 20)
+                torch.cuda.synchronize()
+                row[pn] = {"status": st["status"], "iterations": st["iterations"], "relres": st["relres"],
+                           "solve_ms": round(st["solve_ms"], 2), "update_us": round(1e3 * ms[1], 2),
+                           "iter_us": round(1e3 * sum(ms), 2),
+                           "x_err": float((x - ref).norm() / ref.norm())}
+            print(json.dumps(row), flush=True)
+        del A, d
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.profile_kernels:
@@ -581,6 +645,9 @@ def main():
         return
     if args.sweep == "rhs":
         run_sweep_rhs()
+        return
+    if args.sweep == "precond":
+        run_sweep_precond()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

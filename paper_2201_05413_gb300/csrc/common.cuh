@@ -109,7 +109,7 @@ int num_sms();
 #define GB_TMA_BLOCKS_PER_SM 4
 #endif
 constexpr int TMA_BLOCKS_PER_SM = GB_TMA_BLOCKS_PER_SM;
-// the fp32/bf16 SpMV (smaller shared-memory ring) runs 5 blocks per SM
+// the fp32 SpMV (smaller shared-memory ring) runs 5 blocks per SM
 constexpr int TMA_BLOCKS_PER_SM_NARROW = 5;
 // Grid for a grid-stride kernel: a multiple of the SM count, at most `want`.
 inline int stride_grid(int64_t work_items, int block, int per_sm) {

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) k_spmv_tma(SellView A, const int32_t *__re
 }
 
 template <class TV, class TX, class TI>
-static void launch_spmv_tma_t(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+static void launch_spmv_tma_t(const SellViewH &A, const TV *val, const TX *p, TX *q, double *partials,
                               PcgScal *S, cudaStream_t st) {
     static bool attr_set = false;  // per instantiation
     const int smem = (int)tma_smem_bytes<TV, TI>();
@@ -78,17 +78,18 @@ static void launch_spmv_tma_t(const SellView &A, const TV *val, const TX *p, TX 
     }
     // the warp partition of k_spmv_tma2 for the same value type, so that both
     // index widths sum p.q in the same order
-    const bool narrow = sizeof(TV) < 8 && A.warp_chunk5;
+    const bool narrow = sizeof(TV) == 4 && A.warp_chunk5;
     const int32_t *wchunk = narrow ? A.warp_chunk5 : A.warp_chunk;
     const int grid = (narrow ? A.nwarps5 : A.nwarps) / TMA_WARPS;
     ::gb::count_launches(1); k_spmv_tma<TV, TX, TI><<<grid, NT, smem, st>>>(A, wchunk, val, p, q, partials, S);
 }
 
 // q = A p with the second streaming loop (32-bit indices, spmv_tma.cuh), one
-// warp per balanced chunk range, then the p.q reduction and alpha.
+// warp per chunk range of wchunk (balanced), then the p.q reduction and alpha.
+// The fp32 kernel runs 5 blocks per SM on its own partition (2-deep ring); the
+// fp64 (2-deep) and bf16 (3-deep) kernels 4 blocks per SM.
 template <class TV, class TX>
-__global__ void __launch_bounds__(NT, (sizeof(TV) < 8 ? TMA_BLOCKS_PER_SM_NARROW : TMA_BLOCKS_PER_SM))
-    k_spmv_tma2(SellView A, const int32_t *__restrict__ wchunk,
+__global__ void __launch_bounds__(NT) k_spmv_tma2(SellView A, const int32_t *__restrict__ wchunk,
                                                   const TV *__restrict__ val, const TX *__restrict__ p,
                                                   TX *__restrict__ q, double *partials, PcgScal *S) {
     if (S->done) {
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(NT, (sizeof(TV) < 8 ? TMA_BLOCKS_PER_SM_NARROW
 }
 
 template <class TV, class TX>
-static void launch_spmv_tma2(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+static void launch_spmv_tma2(const SellViewH &A, const TV *val, const TX *p, TX *q, double *partials,
                              PcgScal *S, cudaStream_t st) {
     static bool attr_set = false;  // per instantiation
     const int smem = (int)tma2_smem_bytes<TV>();
@@ -135,8 +136,8 @@ static void launch_spmv_tma2(const SellView &A, const TV *val, const TX *p, TX *
         cudaFuncSetAttribute(k_spmv_tma2<TV, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr_set = true;
     }
-    // fp64 (48 KB ring per block): 4 blocks per SM; fp32/bf16: 5 blocks per SM
-    const bool narrow = sizeof(TV) < 8 && A.warp_chunk5;
+    // fp32 (32 KB ring per block): 5 blocks per SM; fp64 (48 KB), bf16 (36 KB): 4
+    const bool narrow = sizeof(TV) == 4 && A.warp_chunk5;
     const int32_t *wchunk = narrow ? A.warp_chunk5 : A.warp_chunk;
     const int grid = (narrow ? A.nwarps5 : A.nwarps) / TMA_WARPS;
     ::gb::count_launches(1); k_spmv_tma2<TV, TX><<<grid, NT, smem, st>>>(A, wchunk, val, p, q, partials, S);
@@ -145,7 +146,7 @@ static void launch_spmv_tma2(const SellView &A, const TV *val, const TX *p, TX *
 // 16-bit column deltas when the matrix has them (first streaming loop), 32-bit
 // indices otherwise (second streaming loop)
 template <class TV, class TX>
-static void launch_spmv_tma(const SellView &A, const TV *val, const TX *p, TX *q, double *partials,
+static void launch_spmv_tma(const SellViewH &A, const TV *val, const TX *p, TX *q, double *partials,
                             PcgScal *S, cudaStream_t st) {
 #ifndef GB_TMA_NO_COL16
     if (A.col16) launch_spmv_tma_t<TV, TX, int16_t>(A, val, p, q, partials, S, st);
@@ -547,7 +548,7 @@ static Grids pick_grids(int64_t n, int C) {
 }
 
 template <class TV, class TX, class TD>
-static void enqueue_iteration(const SellView &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
+static void enqueue_iteration(const SellViewH &A, const TV *val, const TD *dinv, TX *x, TX *r, TX *p,
                               TX *q, TX *z, double *partials, PcgScal *S, const Grids &g, cudaStream_t st,
                               int variant = 0, const BjView *bj = nullptr) {
     if (variant == 0 && A.C == 32 && A.warp_chunk) launch_spmv_tma<TV, TX>(A, val, p, q, partials, S, st);
@@ -707,7 +708,7 @@ struct Work {
 using namespace gb;
 
 static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_t st, PcgStats *stats) {
-    const SellView V = A->view();
+    const SellViewH V = A->view();
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);
     int64_t launches = 0;
@@ -772,7 +773,7 @@ static int solve_f64(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_
 template <class TV>
 static int solve_ir(const gb_sell *A, const TV *val_in, const PcgOptions &o, Work &w, cudaStream_t st,
                     PcgStats *stats) {
-    const SellView V = A->view();
+    const SellViewH V = A->view();
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);
     int64_t launches = 0;
@@ -867,7 +868,7 @@ template <class TV>
 static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Work &w, cudaStream_t st,
                     PcgStats *stats) {
     constexpr double RU_DELTA = 0.1;
-    const SellView V = A->view();
+    const SellViewH V = A->view();
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);
     Mem &mem = w.mem;
@@ -1063,7 +1064,7 @@ static int kernel_times_impl(const gb_sell *A, const double *d_b, int precision,
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);
-    const SellView V = A->view();
+    const SellViewH V = A->view();
     Work w;
     w.mem = Mem(nullptr, st);
     GB_TRY(w.mem.alloc_n(&w.x, n));

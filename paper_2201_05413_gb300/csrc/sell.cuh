@@ -22,8 +22,16 @@ struct SellView {
     const int32_t *warp_chunk;  // nwarps+1 chunk bounds, balanced by padded nonzeros (C == 32)
     int nwarps;
     const int16_t *col16;       // column - min(row, n-1) per padded slot, or null (C == 32)
-    const int32_t *warp_chunk5; // the same for the 5-blocks-per-SM grid of the fp32/bf16 SpMV
-    int nwarps5;
+};
+
+// Host-side view: the kernel view plus the warp partition of the fp32
+// SpMV's 5-blocks-per-SM grid, passed to that kernel as its own argument.
+// (Kept out of SellView: every kernel takes SellView by value, and a larger
+// SellView changed the fp64 SpMV's code -- 54 instead of 52 registers -- and
+// slowed it from 120 to 137-142 us on 2D P2 1024^2.)
+struct SellViewH : SellView {
+    const int32_t *warp_chunk5 = nullptr;
+    int nwarps5 = 0;
 };
 
 // Block-Jacobi data of a matrix (bjacobi.cuh), passed by value to kernels.
@@ -59,9 +67,13 @@ struct gb_sell {
     float *val32 = nullptr, *dinv32 = nullptr;
     __nv_bfloat16 *val16 = nullptr;
     gb::Mem mem;
-    gb::SellView view() const {
-        return gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16, dinv, dinv32,
-                            chunk_w, warp_chunk, nwarps, col16, warp_chunk5, nwarps5};
+    gb::SellViewH view() const {
+        gb::SellViewH v;
+        static_cast<gb::SellView &>(v) = gb::SellView{n, nchunks, C, chunk_ptr, row_len, col, val, val32, val16,
+                                                      dinv, dinv32, chunk_w, warp_chunk, nwarps, col16};
+        v.warp_chunk5 = warp_chunk5;
+        v.nwarps5 = nwarps5;
+        return v;
     }
     gb::BjView bj_view() const {
         gb::BjView b;

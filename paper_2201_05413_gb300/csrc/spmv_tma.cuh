@@ -261,6 +261,9 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
 #ifndef GB_TMA2_NB32
 #define GB_TMA2_NB32 2
 #endif
+#ifndef GB_TMA2_NB16
+#define GB_TMA2_NB16 3
+#endif
 #ifndef GB_TMA2_SJ64
 #define GB_TMA2_SJ64 8
 #endif
@@ -273,7 +276,7 @@ __device__ __forceinline__ TX spmv_warp_stream(const SellView &A, const TV *__re
 
 template <class TV> struct Tma2Cfg {
     static constexpr int SJ = sizeof(TV) == 8 ? GB_TMA2_SJ64 : GB_TMA2_SJ32;
-    static constexpr int NB = sizeof(TV) == 8 ? GB_TMA2_NB64 : GB_TMA2_NB32;
+    static constexpr int NB = sizeof(TV) == 8 ? GB_TMA2_NB64 : (sizeof(TV) == 4 ? GB_TMA2_NB32 : GB_TMA2_NB16);
 };
 
 template <class TV>
