@@ -72,6 +72,9 @@ def lib():
         L.orc_bjacobi.restype = C.c_int
         L.orc_bjacobi.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p]
         L.orc_bjacobi_apply.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p]
+        L.orc_block_cg.restype = C.c_int
+        L.orc_block_cg.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p, f64p, C.c_double, C.c_int64,
+                                   i64p, f64p]
         L.orc_cholesky_solve.restype = C.c_int
         L.orc_cholesky_solve.argtypes = [C.c_int64, i64p, i32p, f64p, f64p, f64p]
         L.orc_sell_size.argtypes = [C.c_int64, i64p, C.c_int, C.c_int, i64p, i64p]
@@ -221,6 +224,22 @@ def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None):
     A = (n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double))
     st = lib().orc_pcg(*A, *args) if bs is None else lib().orc_pcg_bj(*A, int(bs), *args)
     return x, int(st), int(it[0]), float(rr[0])
+
+
+def block_cg(rp, ci, v, B, tol=1e-10, maxit=None, X0=None):
+    """Block CG (breakdown-free, Jacobi-preconditioned) for A X = B, B (n, k).
+    Returns (X, status, iters, relres per column)."""
+    n = len(rp) - 1
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(n, -1))
+    k = B.shape[1]
+    X = np.zeros((n, k)) if X0 is None else np.array(X0, dtype=np.float64).reshape(n, k)
+    it = np.zeros(1, np.int64)
+    rel = np.zeros(k)
+    maxit = 20 * n + 100 if maxit is None else maxit
+    st = lib().orc_block_cg(n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double), k,
+                            _p(B.reshape(-1), C.c_double), _p(X.reshape(-1), C.c_double), tol, maxit,
+                            _p(it, C.c_int64), _p(rel, C.c_double))
+    return X, int(st), int(it[0]), rel
 
 
 def bjacobi(rp, ci, v, bs):

@@ -738,6 +738,260 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     return st;
 }
 
+/* ------------------------------------------------------------ block CG -- */
+/* The multi-RHS system A X = B of Sec. 4.3 (B: the block of right-hand sides,
+ * n x k, row-major here) solved by block conjugate gradients: one Krylov
+ * space shared by all columns (O'Leary 1980), in the breakdown-free form of
+ * Ji and Li (2017) -- the search block P is orthonormalised with a rank test
+ * each step, so dependent directions (rank-deficient B, columns that converge
+ * at different rates) are dropped instead of making P^T A P singular.
+ * Preconditioner: Jacobi, M = diag(A).  Per step:
+ *   Q = A P;  alpha = (P^T Q)^{-1} P^T R;  X += P alpha;  R -= Q alpha;
+ *   stop when every column has ||R_j|| <= tol ||B_j|| (Eq. 2 per column);
+ *   Z = M^{-1} R;  beta = -(P^T Q)^{-1} Q^T Z;  W = Z + P beta;  P = orth(W).
+ * orth: the columns of W are first scaled by 1/||R_j|| (columns already below
+ * tol are left out), so that the rank test sees directions, not residual
+ * sizes; then with W^T W = V diag(lambda) V^T (cyclic Jacobi), the directions
+ * with lambda_i > 1e-12 lambda_max are kept: P = W V_s diag(lambda_s)^{-1/2}.
+ * At a stop on the recursive residuals the true residual B - A X is formed;
+ * columns above tol restart the recurrence from it. */
+
+/* eigen-decomposition of a symmetric m x m matrix (row-major, destroyed) by
+ * cyclic Jacobi rotations: A = V diag(w) V^T, V's columns the eigenvectors */
+static void sym_eig(int m, double *A, double *w, double *V) {
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) V[i * m + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                tot += A[i * m + j] * A[i * m + j];
+                if (i != j) off += A[i * m + j] * A[i * m + j];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                /* rotation angle zeroing A_pq: tan(2 t) = 2 A_pq / (A_qq - A_pp) */
+                const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int r = 0; r < m; ++r) { /* A <- A J (columns p, q) */
+                    const double arp = A[r * m + p], arq = A[r * m + q];
+                    A[r * m + p] = c * arp - sn * arq;
+                    A[r * m + q] = sn * arp + c * arq;
+                }
+                for (int r = 0; r < m; ++r) { /* A <- J^T A (rows p, q) */
+                    const double apr = A[p * m + r], aqr = A[q * m + r];
+                    A[p * m + r] = c * apr - sn * aqr;
+                    A[q * m + r] = sn * apr + c * aqr;
+                }
+                for (int r = 0; r < m; ++r) { /* V <- V J */
+                    const double vrp = V[r * m + p], vrq = V[r * m + q];
+                    V[r * m + p] = c * vrp - sn * vrq;
+                    V[r * m + q] = sn * vrp + c * vrq;
+                }
+            }
+    }
+    for (int i = 0; i < m; ++i) w[i] = A[i * m + i];
+}
+
+/* C (a x c) = U^T V for row-major U (n x a), V (n x c) */
+static void gram(int64_t n, int a, int c, const double *U, int su, const double *V, int sv, double *C) {
+    for (int i = 0; i < a * c; ++i) C[i] = 0.0;
+    for (int64_t r = 0; r < n; ++r)
+        for (int i = 0; i < a; ++i)
+            for (int j = 0; j < c; ++j) C[i * c + j] += U[r * su + i] * V[r * sv + j];
+}
+
+/* Y (n x k) = A X column by column */
+static void block_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int k,
+                       const double *X, double *Y) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < k; ++j) {
+            double t = 0.0;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) t += v[e] * X[(int64_t)ci[e] * k + j];
+            Y[i * k + j] = t;
+        }
+}
+
+/* P (n x s, leading columns of n x k) = orth(W) with column weights cw (0 =
+ * column left out); returns s */
+static int orth_block(int64_t n, int k, const double *W, const double *cw, double *P) {
+    double *G = (double *)malloc(sizeof(double) * k * k);
+    double *V = (double *)malloc(sizeof(double) * k * k);
+    double *w = (double *)malloc(sizeof(double) * k);
+    double *T = (double *)malloc(sizeof(double) * k * k);
+    int *ord = (int *)malloc(sizeof(int) * k);
+    gram(n, k, k, W, k, W, k, G);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) G[i * k + j] *= cw[i] * cw[j];
+    sym_eig(k, G, w, V);
+    for (int i = 0; i < k; ++i) ord[i] = i;
+    for (int i = 1; i < k; ++i) { /* descending eigenvalues, stable */
+        int t = ord[i], j = i;
+        while (j > 0 && w[ord[j - 1]] < w[t]) { ord[j] = ord[j - 1]; --j; }
+        ord[j] = t;
+    }
+    const double lmax = k > 0 ? w[ord[0]] : 0.0;
+    int s = 0;
+    if (lmax > 0.0)
+        while (s < k && w[ord[s]] > 1e-12 * lmax) ++s;
+    /* T (k x s): column j = cw .* V[:, ord[j]] / sqrt(lambda) */
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < s; ++j) T[i * s + j] = cw[i] * V[i * k + ord[j]] / sqrt(w[ord[j]]);
+    for (int64_t r = 0; r < n; ++r)
+        for (int j = 0; j < k; ++j) {
+            double t = 0.0;
+            if (j < s)
+                for (int i = 0; i < k; ++i) t += W[r * k + i] * T[i * s + j];
+            P[r * k + j] = t;
+        }
+    free(G); free(V); free(w); free(T); free(ord);
+    return s;
+}
+
+/* in-place Cholesky of an s x s SPD matrix (leading block, row stride ld) and
+ * solve for nrhs columns of Y (s x nrhs, row stride ldy) */
+static int chol_solve_small(int s, double *L, int ld, double *Y, int ldy, int nrhs) {
+    for (int j = 0; j < s; ++j) {
+        double d = L[j * ld + j];
+        for (int q = 0; q < j; ++q) d -= L[j * ld + q] * L[j * ld + q];
+        if (!(d > 0.0)) return 1;
+        d = sqrt(d);
+        L[j * ld + j] = d;
+        for (int i = j + 1; i < s; ++i) {
+            double t = L[i * ld + j];
+            for (int q = 0; q < j; ++q) t -= L[i * ld + q] * L[j * ld + q];
+            L[i * ld + j] = t / d;
+        }
+    }
+    for (int c = 0; c < nrhs; ++c) {
+        for (int i = 0; i < s; ++i) {
+            double t = Y[i * ldy + c];
+            for (int q = 0; q < i; ++q) t -= L[i * ld + q] * Y[q * ldy + c];
+            Y[i * ldy + c] = t / L[i * ld + i];
+        }
+        for (int i = s - 1; i >= 0; --i) {
+            double t = Y[i * ldy + c];
+            for (int q = i + 1; q < s; ++q) t -= L[q * ld + i] * Y[q * ldy + c];
+            Y[i * ldy + c] = t / L[i * ld + i];
+        }
+    }
+    return 0;
+}
+
+int orc_block_cg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int k,
+                 const double *B, double *X, double tol, int64_t maxit, int64_t *iters,
+                 double *relres) {
+    *iters = 0;
+    if (k < 1) return 2;
+    const size_t nk = (size_t)(n > 0 ? n : 1) * k;
+    double *dinv = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *R = (double *)malloc(sizeof(double) * nk), *Z = (double *)malloc(sizeof(double) * nk);
+    double *W = (double *)malloc(sizeof(double) * nk), *P = (double *)malloc(sizeof(double) * nk);
+    double *Q = (double *)malloc(sizeof(double) * nk);
+    double *bn = (double *)malloc(sizeof(double) * k), *rn = (double *)malloc(sizeof(double) * k);
+    double *cw = (double *)malloc(sizeof(double) * k);
+    double *PtQ = (double *)malloc(sizeof(double) * k * k), *L = (double *)malloc(sizeof(double) * k * k);
+    double *al = (double *)malloc(sizeof(double) * k * k);
+    for (int64_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) if (ci[e] == i) d = v[e];
+        dinv[i] = 1.0 / d;
+    }
+    for (int j = 0; j < k; ++j) {
+        double t = 0.0;
+        for (int64_t i = 0; i < n; ++i) t += B[i * k + j] * B[i * k + j];
+        bn[j] = sqrt(t);
+    }
+    int status = 1, restarts = 0;
+    int64_t it = 0;
+#define COLREL(j) (bn[j] > 0.0 ? rn[j] / bn[j] : rn[j])
+    for (;;) {
+        /* true residual R = B - A X, column norms */
+        block_spmv(n, rp, ci, v, k, X, Q);
+        for (size_t e = 0; e < (size_t)n * k; ++e) R[e] = B[e] - Q[e];
+        double worst = 0.0;
+        for (int j = 0; j < k; ++j) {
+            double t = 0.0;
+            for (int64_t i = 0; i < n; ++i) t += R[i * k + j] * R[i * k + j];
+            rn[j] = sqrt(t);
+            if (COLREL(j) > worst) worst = COLREL(j);
+        }
+        if (worst <= tol) { status = 0; break; }
+        if (it >= maxit || restarts > 50) break;
+        if (it > 0) ++restarts;
+        /* Z = M^-1 R, P = orth(Z) */
+        for (int64_t i = 0; i < n; ++i)
+            for (int j = 0; j < k; ++j) Z[i * k + j] = dinv[i] * R[i * k + j];
+        for (int j = 0; j < k; ++j) cw[j] = COLREL(j) > tol ? 1.0 / rn[j] : 0.0;
+        int s = orth_block(n, k, Z, cw, P);
+        int restart = 0;
+        while (it < maxit && !restart) {
+            if (s == 0) { status = 2; break; }
+            block_spmv(n, rp, ci, v, k, P, Q); /* columns >= s of P are 0 */
+            gram(n, s, s, P, k, Q, k, PtQ);
+            gram(n, s, k, P, k, R, k, al);
+            for (int e = 0; e < s * s; ++e) L[e] = PtQ[e];
+            if (chol_solve_small(s, L, s, al, k, k)) { status = 2; break; }
+            for (int64_t i = 0; i < n; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double dx = 0.0, dr = 0.0;
+                    for (int q = 0; q < s; ++q) {
+                        dx += P[i * k + q] * al[q * k + j];
+                        dr += Q[i * k + q] * al[q * k + j];
+                    }
+                    X[i * k + j] += dx;
+                    R[i * k + j] -= dr;
+                }
+            ++it;
+            double worst2 = 0.0;
+            for (int j = 0; j < k; ++j) {
+                double t = 0.0;
+                for (int64_t i = 0; i < n; ++i) t += R[i * k + j] * R[i * k + j];
+                rn[j] = sqrt(t);
+                if (COLREL(j) > worst2) worst2 = COLREL(j);
+            }
+            if (worst2 <= tol) { restart = 1; break; } /* confirm on the true residual */
+            for (int64_t i = 0; i < n; ++i)
+                for (int j = 0; j < k; ++j) Z[i * k + j] = dinv[i] * R[i * k + j];
+            /* beta = -(P^T Q)^-1 Q^T Z (the factor of P^T Q is still in L) */
+            gram(n, s, k, Q, k, Z, k, al);
+            for (int e = 0; e < s * k; ++e) al[e] = -al[e];
+            for (int c = 0; c < k; ++c) { /* reuse the factor: two triangular solves */
+                for (int i = 0; i < s; ++i) {
+                    double t = al[i * k + c];
+                    for (int q = 0; q < i; ++q) t -= L[i * s + q] * al[q * k + c];
+                    al[i * k + c] = t / L[i * s + i];
+                }
+                for (int i = s - 1; i >= 0; --i) {
+                    double t = al[i * k + c];
+                    for (int q = i + 1; q < s; ++q) t -= L[q * s + i] * al[q * k + c];
+                    al[i * k + c] = t / L[i * s + i];
+                }
+            }
+            for (int64_t i = 0; i < n; ++i)
+                for (int j = 0; j < k; ++j) {
+                    double t = Z[i * k + j];
+                    for (int q = 0; q < s; ++q) t += P[i * k + q] * al[q * k + j];
+                    W[i * k + j] = t;
+                }
+            for (int j = 0; j < k; ++j) cw[j] = COLREL(j) > tol ? 1.0 / rn[j] : 0.0;
+            s = orth_block(n, k, W, cw, P);
+        }
+        if (status == 2) break;
+        if (!restart) break; /* maxit */
+    }
+#undef COLREL
+    for (int j = 0; j < k; ++j) relres[j] = bn[j] > 0.0 ? rn[j] / bn[j] : rn[j];
+    *iters = it;
+    free(dinv); free(R); free(Z); free(W); free(P); free(Q); free(bn); free(rn); free(cw);
+    free(PtQ); free(L); free(al);
+    return status;
+}
+
 /* ----------------------------------------------------------- SELL-C-sigma -- */
 /* Rows are cut into windows of sigma consecutive rows; inside a window they are
  * ordered by descending row length, ties kept in original order (stable).  The

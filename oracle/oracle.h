@@ -94,6 +94,17 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
                double *relres);
 
+/* Block CG for A X = B (Sec. 4.3's block of right-hand sides; B, X n x k
+ * row-major, X in: X0, out: X): one shared Krylov space (O'Leary), in the
+ * breakdown-free form of Ji and Li (rank-revealing orthonormalisation of the
+ * search block), Jacobi preconditioner.  Stops when every column meets Eq. (2)
+ * on the true residual; relres[k] receives the final relative residuals.
+ * Returns 0 converged, 1 not converged in maxit steps, 2 breakdown (no
+ * search direction left above the rank threshold, or P^T A P not SPD). */
+int orc_block_cg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int k,
+                 const double *B, double *X, double tol, int64_t maxit, int64_t *iters,
+                 double *relres);
+
 /* Dense Cholesky solve A x = b (n small).  Returns 0, or 1 if A is not SPD. */
 int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                        const double *b, double *x);
