@@ -300,6 +300,25 @@ int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_
                       double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                       PcgStats *stats);
 
+/* Block CG for A X = B (Sec. 4.3, Eq. MRH: the k right-hand sides known
+ * together): one Krylov space shared by the k columns (O'Leary's block
+ * conjugate gradients) in a breakdown-free form -- the search block is
+ * orthonormalised every step with a rank test (eigenvalues of its Gram
+ * matrix, columns scaled by their residual norms, below a relative threshold
+ * dropped), so a rank-deficient B or columns converging at different rates
+ * reduce the block instead of breaking the recurrence.  Jacobi
+ * preconditioner.  d_B, d_X: n x k row-major in the original free-dof order
+ * (d_X in: x0 unless x0_zero, out: X), 1 <= k <= 32.  precision GB_F64 (the
+ * recurrence in fp64, restarted from the true residual until every column
+ * meets Eq. 2) or GB_F32_IR (fp32 block recurrence on the column-scaled fp64
+ * residual to inner_tol, fp64 refinement outside).  stats (one for the
+ * block): iterations = block steps, outer = refinement steps, relres = the
+ * largest column relative residual, status GB_OK / GB_NOT_CONVERGED /
+ * GB_BREAKDOWN.  Synchronises `stream` (the k x k algebra runs on the host,
+ * three round trips per step). */
+int pcg_solve_block(const gb_sell *A, const double *d_B, double *d_X, int k, const PcgOptions *opt,
+                    void *stream, PcgStats *stats);
+
 /* ------------------------------------------------------------- serving --
  * A solve server with continuous batching.  Requests (mesh spec, k right-
  * hand sides) are admitted as resident "slots" while max_slots and the device

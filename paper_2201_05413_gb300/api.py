@@ -192,6 +192,20 @@ class Sell:
                 "sell_spmv")
         return y
 
+    def solve_block(self, B, X0=None, raise_on_fail=True, stream=None, **kw):
+        """pcg_solve_block: block CG for the n x k block B (k <= 32); returns (X, stats dict)."""
+        B = (B if B.dim() == 2 else B.reshape(-1, 1)).contiguous()
+        X = X0.clone().contiguous() if X0 is not None else torch.empty_like(B)
+        o = _opts(x0_zero=0 if X0 is not None else 1, **kw)
+        st = G.PcgStats()
+        rc = G.lib().pcg_solve_block(self.handle, G.ptr(B), G.ptr(X), B.shape[1], C.byref(o),
+                                     G.stream_ptr(stream if stream is not None else self._stream), C.byref(st))
+        if raise_on_fail:
+            G.check(rc, "pcg_solve_block")
+        d = st.as_dict()
+        d["rc"] = rc
+        return X, d
+
     def block_jacobi(self, bs, stream=None):
         """sell_block_jacobi: attaches the block-Jacobi inverses (bs = 0 detaches them)."""
         G.check(G.lib().sell_block_jacobi(self.handle, int(bs),

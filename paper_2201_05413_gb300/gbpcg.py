@@ -153,6 +153,7 @@ _SIGS = {
     "serve_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ServeResult)]),
     "serve_stats": (C.c_int, [_P, C.POINTER(ServeStats)]),
     "serve_destroy": (None, [_P]),
+    "pcg_solve_block": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_solve_batched": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                     C.POINTER(C.c_int), C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "gbpcg_wait_selftest": (C.c_int, [C.c_double, _P, C.POINTER(C.c_double)]),
