@@ -72,6 +72,9 @@ def lib():
         L.orc_bjacobi.restype = C.c_int
         L.orc_bjacobi.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p]
         L.orc_bjacobi_apply.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p]
+        L.orc_bicgstab.restype = C.c_int
+        L.orc_bicgstab.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p, f64p, C.c_double, C.c_int64,
+                                   i64p, f64p]
         L.orc_block_cg.restype = C.c_int
         L.orc_block_cg.argtypes = [C.c_int64, i64p, i32p, f64p, C.c_int, f64p, f64p, C.c_double, C.c_int64,
                                    i64p, f64p]
@@ -223,6 +226,21 @@ def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None):
     args = (_p(b, C.c_double), _p(x, C.c_double), tol, maxit, _p(it, C.c_int64), _p(rr, C.c_double))
     A = (n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double))
     st = lib().orc_pcg(*A, *args) if bs is None else lib().orc_pcg_bj(*A, int(bs), *args)
+    return x, int(st), int(it[0]), float(rr[0])
+
+
+def bicgstab(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=0):
+    """Right-preconditioned BiCGSTAB (Jacobi for bs <= 1, block-Jacobi over bs
+    rows otherwise).  Returns (x, status, iters, relres)."""
+    n = len(rp) - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    it = np.zeros(1, np.int64)
+    rr = np.zeros(1)
+    maxit = 20 * n + 100 if maxit is None else maxit
+    st = lib().orc_bicgstab(n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double), int(bs),
+                            _p(b, C.c_double), _p(x, C.c_double), tol, maxit, _p(it, C.c_int64),
+                            _p(rr, C.c_double))
     return x, int(st), int(it[0]), float(rr[0])
 
 

@@ -738,6 +738,114 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
     return st;
 }
 
+/* ------------------------------------------------------------ BiCGSTAB -- */
+/* BiCGSTAB (van der Vorst 1992), the Krylov method the paper runs (Sec. 3.1),
+ * with the preconditioner applied on the right (x = M^{-1} y):
+ *   r = b - A x, rh = r (shadow residual), rho0 = alpha = omega = 1, p = v = 0
+ *   repeat: rho = rh.r; beta = (rho/rho0)(alpha/omega);
+ *           p = r + beta (p - omega v); ph = M^{-1} p; v = A ph;
+ *           alpha = rho / rh.v; s = r - alpha v;
+ *           if ||s|| <= tol ||b||: x += alpha ph, stop;
+ *           sh = M^{-1} s; t = A sh; omega = t.s / t.t;
+ *           x += alpha ph + omega sh; r = s - omega t;
+ *           stop if ||r|| <= tol ||b|| (Eq. 2); rho0 = rho.
+ * A stop is confirmed on the true residual; above tol the recurrence restarts
+ * from it (new shadow residual).  Breakdown: rh.v, t.t or rho = 0. */
+static int bicgstab_core(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
+                         precond_fn apply, const void *ctx, const double *b, double *x, double tol,
+                         int64_t maxit, int64_t *iters, double *relres) {
+    *iters = 0;
+    const double bn = sqrt(dot(n, b, b));
+    if (bn == 0.0) {
+        for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+        *relres = 0.0;
+        return 0;
+    }
+    const size_t sz = sizeof(double) * (n > 0 ? n : 1);
+    double *r = (double *)malloc(sz), *rh = (double *)malloc(sz), *p = (double *)malloc(sz);
+    double *vv = (double *)malloc(sz), *ph = (double *)malloc(sz), *sv = (double *)malloc(sz);
+    double *sh = (double *)malloc(sz), *t = (double *)malloc(sz);
+    int status = 1, restarts = 0;
+    int64_t it = 0;
+    double rel = 0.0;
+    for (;;) {
+        orc_spmv(n, rp, ci, v, x, t);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        rel = sqrt(dot(n, r, r)) / bn;
+        if (rel <= tol) { status = 0; break; }
+        if (it >= maxit || restarts > 50) break;
+        if (it > 0) ++restarts;
+        for (int64_t i = 0; i < n; ++i) { rh[i] = r[i]; p[i] = 0.0; vv[i] = 0.0; }
+        double rho0 = 1.0, alpha = 1.0, omega = 1.0;
+        int stop = 0;
+        while (it < maxit) {
+            const double rho = dot(n, rh, r);
+            if (rho == 0.0 || !isfinite(rho)) { status = 2; break; }
+            const double beta = (rho / rho0) * (alpha / omega);
+            for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * vv[i]);
+            apply(n, ctx, p, ph);
+            orc_spmv(n, rp, ci, v, ph, vv);
+            const double rv = dot(n, rh, vv);
+            if (rv == 0.0 || !isfinite(rv)) { status = 2; break; }
+            alpha = rho / rv;
+            for (int64_t i = 0; i < n; ++i) sv[i] = r[i] - alpha * vv[i];
+            ++it;
+            if (sqrt(dot(n, sv, sv)) / bn <= tol) {
+                for (int64_t i = 0; i < n; ++i) x[i] += alpha * ph[i];
+                stop = 1;
+                break;
+            }
+            apply(n, ctx, sv, sh);
+            orc_spmv(n, rp, ci, v, sh, t);
+            const double tt = dot(n, t, t);
+            if (tt == 0.0 || !isfinite(tt)) { status = 2; break; }
+            omega = dot(n, t, sv) / tt;
+            for (int64_t i = 0; i < n; ++i) {
+                x[i] += alpha * ph[i] + omega * sh[i];
+                r[i] = sv[i] - omega * t[i];
+            }
+            if (sqrt(dot(n, r, r)) / bn <= tol) { stop = 1; break; }
+            if (omega == 0.0) { status = 2; break; }
+            rho0 = rho;
+        }
+        if (status == 2 || !stop) break;
+    }
+    if (status != 0) { /* report the true residual of the x returned */
+        orc_spmv(n, rp, ci, v, x, t);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+        rel = sqrt(dot(n, r, r)) / bn;
+    }
+    *iters = it;
+    *relres = rel;
+    free(r); free(rh); free(p); free(vv); free(ph); free(sv); free(sh); free(t);
+    return status;
+}
+
+int orc_bicgstab(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+                 const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
+                 double *relres) {
+    *iters = 0;
+    *relres = 0.0;
+    if (bs <= 1) { /* Jacobi (bs 0 or 1: the same M) */
+        double *dinv = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) {
+            double d = 0.0;
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) if (ci[k] == i) d = v[k];
+            dinv[i] = 1.0 / d;
+        }
+        const int st = bicgstab_core(n, rp, ci, v, jacobi_apply, dinv, b, x, tol, maxit, iters, relres);
+        free(dinv);
+        return st;
+    }
+    const int64_t nblk = (n + bs - 1) / bs;
+    double *W = (double *)malloc(sizeof(double) * (nblk > 0 ? nblk : 1) * bs * bs);
+    if (orc_bjacobi(n, rp, ci, v, bs, W)) { free(W); return 2; }
+    struct bj_ctx c = {bs, W};
+    const int st = bicgstab_core(n, rp, ci, v, bjacobi_apply_cb, &c, b, x, tol, maxit, iters, relres);
+    free(W);
+    return st;
+}
+
 /* ------------------------------------------------------------ block CG -- */
 /* The multi-RHS system A X = B of Sec. 4.3 (B: the block of right-hand sides,
  * n x k, row-major here) solved by block conjugate gradients: one Krylov

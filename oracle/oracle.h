@@ -94,6 +94,15 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
                double *relres);
 
+/* BiCGSTAB (Sec. 3.1's Krylov method), right-preconditioned: bs <= 1 Jacobi,
+ * bs >= 2 block-Jacobi over blocks of bs rows (orc_bjacobi).  Any nonsingular
+ * CSR matrix.  Stops on Eq. (2), confirmed on the true residual (restart from
+ * it otherwise).  Returns 0 converged, 1 not converged in maxit steps, 2
+ * breakdown; relres: the true relative residual of the x returned. */
+int orc_bicgstab(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs,
+                 const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
+                 double *relres);
+
 /* Block CG for A X = B (Sec. 4.3's block of right-hand sides; B, X n x k
  * row-major, X in: X0, out: X): one shared Krylov space (O'Leary), in the
  * breakdown-free form of Ji and Li (rank-revealing orthonormalisation of the
