@@ -560,7 +560,8 @@ def run_sweep_rhs():
     """Time to solve k right-hand sides of one system (2D jittered P2 256^2,
     harmonic-basis Dirichlet data), blocked (Eq. MRH: k recurrences sharing one
     SpMM pass, in groups of up to 32 columns per system of the batch) against
-    one pcg_solve per column, fp64 and fp32 recurrences."""
+    one pcg_solve per column, fp64 and fp32 recurrences; for k <= 32 also block
+    CG (one Krylov space shared by the k columns, pcg_solve_block)."""
     import numpy as np
     import torch
     import paper_2201_05413_gb300 as P
@@ -591,7 +592,19 @@ def run_sweep_rhs():
             row[pn] = {"blocked_s": round(tb, 4), "blocked_ms_per_rhs": round(1e3 * tb / k, 3),
                        "one_at_a_time_s": None if ts is None else round(ts, 4),
                        "one_at_a_time_ms_per_rhs": None if ts is None else round(1e3 * ts / k, 3),
-                       "max_relres": max(x["relres"] for x in sts), "status": max(abs(x["status"]) for x in sts)}
+                       "max_relres": max(x["relres"] for x in sts), "status": max(abs(x["status"]) for x in sts),
+                       "iterations_per_column_max": max(x["iterations"] for x in sts)}
+            if k <= 32:  # block CG: one Krylov space shared by the k columns
+                pk = P.GB_F64 if pn == "f64" else P.GB_F32_IR
+                A.solve_block(B, tol=TOL, precision=pk, raise_on_fail=False)  # warm
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, sb = A.solve_block(B, tol=TOL, precision=pk, raise_on_fail=False)
+                torch.cuda.synchronize()
+                tcg = time.perf_counter() - t0
+                row[pn]["block_cg"] = {"s": round(tcg, 4), "ms_per_rhs": round(1e3 * tcg / k, 3),
+                                       "steps": sb["iterations"], "outer": sb["outer"], "relres": sb["relres"],
+                                       "status": sb["status"]}
         print(json.dumps(row), flush=True)
 
 

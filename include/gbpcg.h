@@ -252,6 +252,13 @@ int sell_block_jacobi_apply(const gb_sell *A, const double *d_x, double *d_y, vo
  * pcg_solve_batched and pcg_solve_noalloc). */
 enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2, GB_F32_RU = 3, GB_BF16_RU = 4 };
 enum { GB_PC_JACOBI = 0, GB_PC_BLOCK_JACOBI = 1 };
+/* method GB_BICGSTAB: BiCGSTAB (van der Vorst), the Krylov method of the
+ * paper's experiments (Sec. 3.1), preconditioned on the right with the
+ * Jacobi or block-Jacobi M: two SpMVs and two preconditioner applications per
+ * step (stats.iterations counts steps); the stop is confirmed on the true
+ * residual as for CG.  pcg_solve with GB_F64 on C = 32 layouts (GB_EINVAL
+ * otherwise, and in the batched, block and no-allocation solvers). */
+enum { GB_CG = 0, GB_BICGSTAB = 1 };
 
 typedef struct PcgOptions {
     double tol;            /* Eq. (2) threshold, e.g. 1e-10 */
@@ -269,6 +276,7 @@ typedef struct PcgOptions {
                               power of two >= k) are solved whole by one CTA each in a single
                               persistent launch; 1 = every system in the multi-launch loop */
     int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
+    int32_t method;        /* GB_CG (0, default) or GB_BICGSTAB (pcg_solve, GB_F64, C = 32) */
 } PcgOptions;
 
 typedef struct PcgStats {

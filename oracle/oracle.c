@@ -750,7 +750,9 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
  *           x += alpha ph + omega sh; r = s - omega t;
  *           stop if ||r|| <= tol ||b|| (Eq. 2); rho0 = rho.
  * A stop is confirmed on the true residual; above tol the recurrence restarts
- * from it (new shadow residual).  Breakdown: rh.v, t.t or rho = 0. */
+ * from it (new shadow residual).  Breakdown (rh.v, t.t, rho or omega zero or
+ * not finite) also restarts from the true residual, as long as that residual
+ * is below 0.9 times the one the previous restart started from. */
 static int bicgstab_core(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                          precond_fn apply, const void *ctx, const double *b, double *x, double tol,
                          int64_t maxit, int64_t *iters, double *relres) {
@@ -765,28 +767,31 @@ static int bicgstab_core(int64_t n, const int64_t *rp, const int32_t *ci, const 
     double *r = (double *)malloc(sz), *rh = (double *)malloc(sz), *p = (double *)malloc(sz);
     double *vv = (double *)malloc(sz), *ph = (double *)malloc(sz), *sv = (double *)malloc(sz);
     double *sh = (double *)malloc(sz), *t = (double *)malloc(sz);
-    int status = 1, restarts = 0;
+    int status = 1, restarts = 0, broke = 0;
     int64_t it = 0;
-    double rel = 0.0;
+    double rel = 0.0, rel_start = INFINITY;
     for (;;) {
         orc_spmv(n, rp, ci, v, x, t);
         for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
         rel = sqrt(dot(n, r, r)) / bn;
         if (rel <= tol) { status = 0; break; }
         if (it >= maxit || restarts > 50) break;
+        if (broke && !(rel < 0.9 * rel_start)) { status = 2; break; }
+        broke = 0;
+        rel_start = rel;
         if (it > 0) ++restarts;
         for (int64_t i = 0; i < n; ++i) { rh[i] = r[i]; p[i] = 0.0; vv[i] = 0.0; }
         double rho0 = 1.0, alpha = 1.0, omega = 1.0;
         int stop = 0;
         while (it < maxit) {
             const double rho = dot(n, rh, r);
-            if (rho == 0.0 || !isfinite(rho)) { status = 2; break; }
+            if (rho == 0.0 || !isfinite(rho)) { broke = 1; break; }
             const double beta = (rho / rho0) * (alpha / omega);
             for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * vv[i]);
             apply(n, ctx, p, ph);
             orc_spmv(n, rp, ci, v, ph, vv);
             const double rv = dot(n, rh, vv);
-            if (rv == 0.0 || !isfinite(rv)) { status = 2; break; }
+            if (rv == 0.0 || !isfinite(rv)) { broke = 1; break; }
             alpha = rho / rv;
             for (int64_t i = 0; i < n; ++i) sv[i] = r[i] - alpha * vv[i];
             ++it;
@@ -798,17 +803,17 @@ static int bicgstab_core(int64_t n, const int64_t *rp, const int32_t *ci, const 
             apply(n, ctx, sv, sh);
             orc_spmv(n, rp, ci, v, sh, t);
             const double tt = dot(n, t, t);
-            if (tt == 0.0 || !isfinite(tt)) { status = 2; break; }
+            if (tt == 0.0 || !isfinite(tt)) { broke = 1; break; }
             omega = dot(n, t, sv) / tt;
             for (int64_t i = 0; i < n; ++i) {
                 x[i] += alpha * ph[i] + omega * sh[i];
                 r[i] = sv[i] - omega * t[i];
             }
             if (sqrt(dot(n, r, r)) / bn <= tol) { stop = 1; break; }
-            if (omega == 0.0) { status = 2; break; }
+            if (omega == 0.0 || !isfinite(omega)) { broke = 1; break; }
             rho0 = rho;
         }
-        if (status == 2 || !stop) break;
+        if (!stop && !broke) break; /* maxit */
     }
     if (status != 0) { /* report the true residual of the x returned */
         orc_spmv(n, rp, ci, v, x, t);

@@ -30,9 +30,9 @@ def _view(ptr, shape, dtype):
 
 
 def _opts(tol=1e-10, max_iter=0, precision=G.GB_F64, max_outer=0, inner_tol=0.0, check_every=0,
-          use_graph=1, x0_zero=1, spmv_variant=0, persist_off=0, precond=G.GB_PC_JACOBI):
+          use_graph=1, x0_zero=1, spmv_variant=0, persist_off=0, precond=G.GB_PC_JACOBI, method=G.GB_CG):
     return G.PcgOptions(tol, max_iter, precision, max_outer, inner_tol, check_every, use_graph,
-                        x0_zero, spmv_variant, persist_off, precond)
+                        x0_zero, spmv_variant, persist_off, precond, method)
 
 
 class FemSystem:

@@ -210,6 +210,7 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     if (graphs_disabled()) o.use_graph = 0;
     GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve_batched: bad precision");
     GB_REQUIRE(o.precond == GB_PC_JACOBI, "pcg_solve_batched: the Jacobi preconditioner only");
+    GB_REQUIRE(o.method == GB_CG, "pcg_solve_batched: CG only");
     for (int s = 0; s < nsys; ++s) {
         GB_REQUIRE(o.precision != GB_F32_IR || A[s]->val32, "pcg_solve_batched: system %d has no fp32 values", s);
         GB_REQUIRE(o.precision != GB_BF16_IR || A[s]->val16, "pcg_solve_batched: system %d has no bf16 values", s);

@@ -667,6 +667,7 @@ extern "C" int pcg_solve_block(const gb_sell *A, const double *d_B, double *d_X,
                "pcg_solve_block: precision GB_F64 or GB_F32_IR");
     GB_REQUIRE(o.precision != GB_F32_IR || A->val32, "pcg_solve_block: GB_F32_IR needs fp32 values (val_types)");
     GB_REQUIRE(o.precond == GB_PC_JACOBI, "pcg_solve_block: the Jacobi preconditioner only");
+    GB_REQUIRE(o.method == GB_CG, "pcg_solve_block: block CG (method GB_CG) only");
     cudaStream_t st = (cudaStream_t)stream;
     const int KW = k <= 4 ? 4 : k <= 8 ? 8 : k <= 16 ? 16 : 32;
     switch (KW) {

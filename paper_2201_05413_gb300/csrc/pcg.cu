@@ -19,6 +19,7 @@
 #include <mutex>
 #include <vector>
 
+#include "bicgstab.cuh"
 #include "bjacobi.cuh"
 #include "pcg.cuh"
 #include "spmv_tma.cuh"
@@ -579,7 +580,8 @@ static void enqueue_residual(const SellView &A, const double *x, const double *b
 // of a graph holding a while-node around one iteration; the finishing block
 // clears the condition.  Direct mode: `chunk` iterations per host poll.
 template <class F>
-static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &&enqueue, int64_t *launches) {
+static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &&enqueue, int64_t *launches,
+                    int per_iter = 3) {
     if (use_graph) {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
@@ -623,7 +625,7 @@ static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &
             if (e == cudaSuccess) e = cudaMemcpyAsync(&it1, &dS->it, sizeof(it1), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             // the body ran once per iteration (plus once when it stopped inside SpMV)
-            count_launches(3 * (it1 - it0) + 3);
+            count_launches(per_iter * (it1 - it0) + per_iter);
         }
         if (e != cudaSuccess) { set_error("pcg loop graph: %s", cudaGetErrorString(e)); rc = GB_ECUDA; }
         if (ge) cudaGraphExecDestroy(ge);
@@ -634,7 +636,7 @@ static int run_loop(cudaStream_t st, PcgScal *dS, bool use_graph, int chunk, F &
     }
     for (;;) {
         for (int i = 0; i < chunk; ++i) enqueue(st);
-        if (launches) *launches += 3 * chunk;
+        if (launches) *launches += per_iter * chunk;
         int done = 0;
         GB_CHECK_CUDA(cudaGetLastError());
         GB_CHECK_CUDA(cudaMemcpyAsync(&done, &dS->done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -967,6 +969,105 @@ static int solve_ru(const gb_sell *A, const TV *val_in, const PcgOptions &o, Wor
     return GB_OK;
 }
 
+// BiCGSTAB (bicgstab.cuh), fp64, Jacobi or block-Jacobi on the right; the
+// true residual confirms a stop (restart from it otherwise), as in solve_f64.
+static int solve_bicgstab(const gb_sell *A, const PcgOptions &o, Work &w, cudaStream_t st, PcgStats *stats) {
+    const SellViewH V = A->view();
+    const int64_t n = A->n;
+    const Grids g = pick_grids(n, A->C);
+    const bool use_bj = o.precond == GB_PC_BLOCK_JACOBI;
+    const BjView bj = A->bj_view();
+    int64_t launches = 0;
+    struct Vecs {
+        Mem *m;
+        double *rh = nullptr, *v = nullptr, *ph = nullptr, *s = nullptr, *sh = nullptr, *t = nullptr;
+        ~Vecs() { m->release(rh); m->release(v); m->release(ph); m->release(s); m->release(sh); m->release(t); }
+    } u{&w.mem};
+    GB_TRY(w.mem.alloc_n(&u.rh, n));
+    GB_TRY(w.mem.alloc_n(&u.v, n));
+    GB_TRY(w.mem.alloc_n(&u.ph, n));
+    GB_TRY(w.mem.alloc_n(&u.s, n));
+    GB_TRY(w.mem.alloc_n(&u.sh, n));
+    GB_TRY(w.mem.alloc_n(&u.t, n));
+    enqueue_residual(V, o.x0_zero ? nullptr : w.x, w.b, w.r, w.partials, w.S, 1, o.tol, g, st);
+    ++launches;
+    PcgScal h{};
+    GB_TRY(read_scal(w.S, &h, st));
+    stats->bnorm = std::sqrt(h.bb);
+    if (h.bb == 0.0) {
+        GB_CHECK_CUDA(cudaMemsetAsync(w.x, 0, sizeof(double) * n, st));
+        stats->relres = 0.0;
+        stats->status = GB_OK;
+        stats->kernel_launches = launches + 1;
+        return GB_OK;
+    }
+    static bool attr_set[2] = {false, false};
+    const int smem = (int)tma2_smem_bytes<double>();
+    if (!attr_set[0]) {
+        cudaFuncSetAttribute(k_spmv_bi<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_spmv_bi<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set[0] = attr_set[1] = true;
+    }
+    const int gs = V.nwarps / TMA_WARPS;
+    const int gbj = bj_grid(n);
+    int64_t restarts = 0;
+    int status = ST_RUN;
+    double rel = std::sqrt(h.rr / h.bb);
+    double rel_start = rel;  // true residual the current recurrence started from
+    while (rel > o.tol) {
+        ::gb::count_launches(1); k_bi_start<<<g.vec, NT, 0, st>>>(n, w.r, u.rh, w.p, u.v, w.partials, w.S);
+        ++launches;
+        GB_CHECK_CUDA(cudaGetLastError());
+        auto body = [&](cudaStream_t s) {
+            if (use_bj) {
+#define GB_BI_P(K) ::gb::count_launches(1); k_bi_p_bj<K><<<gbj, BJ_WIN, 0, s>>>(n, w.r, u.v, w.p, u.ph, bj, w.S)
+                GB_BJ_DISPATCH(bj.bs, GB_BI_P)
+#undef GB_BI_P
+            } else {
+                ::gb::count_launches(1); k_bi_p<<<g.upd, NT, 0, s>>>(n, w.r, u.v, w.p, u.ph, A->dinv, w.S);
+            }
+            ::gb::count_launches(1);
+            k_spmv_bi<1><<<gs, NT, smem, s>>>(V, V.warp_chunk, A->val, u.ph, u.v, u.rh, w.partials, w.S);
+            if (use_bj) {
+#define GB_BI_S(K) ::gb::count_launches(1); k_bi_s_bj<K><<<gbj, BJ_WIN, 0, s>>>(n, w.r, u.v, u.s, u.sh, bj, w.partials, w.S)
+                GB_BJ_DISPATCH(bj.bs, GB_BI_S)
+#undef GB_BI_S
+            } else {
+                ::gb::count_launches(1); k_bi_s<<<g.upd, NT, 0, s>>>(n, w.r, u.v, u.s, u.sh, A->dinv, w.partials, w.S);
+            }
+            ::gb::count_launches(1);
+            k_spmv_bi<2><<<gs, NT, smem, s>>>(V, V.warp_chunk, A->val, u.sh, u.t, u.s, w.partials, w.S);
+            ::gb::count_launches(1);
+            k_bi_x<<<g.upd, NT, 0, s>>>(n, w.x, w.r, u.ph, u.sh, u.s, u.t, u.rh, w.partials, w.S);
+        };
+        GB_TRY(run_loop(st, w.S, o.use_graph != 0, o.check_every, body, nullptr, 5));
+        GB_TRY(read_scal(w.S, &h, st));
+        status = h.status;
+        enqueue_residual(V, w.x, w.b, w.r, w.partials, w.S, 0, o.tol, g, st);
+        ++launches;
+        PcgScal h2{};
+        GB_TRY(read_scal(w.S, &h2, st));
+        rel = std::sqrt(h2.rr / h2.bb);
+        if (getenv("GBPCG_LOG"))
+            fprintf(stderr, "[gbpcg bicgstab] stop after %lld steps: status %d (breakdown code %d), true relres %.3e\n",
+                    h.it, status, h.brk, rel);
+        // a stop on the recursive residual above tol, or a breakdown while the
+        // true residual still falls: restart from the true residual
+        const bool retry = status == ST_CONV || (status == ST_BREAK && rel < 0.9 * rel_start);
+        if (!retry || rel <= o.tol || h.it >= h.maxit || ++restarts > 50) break;
+        rel_start = rel;
+    }
+    if (rel <= o.tol) status = ST_CONV;
+    stats->iterations = h.it;
+    stats->restarts = restarts;
+    stats->relres = rel;
+    stats->status = map_status(status);
+    stats->kernel_launches = launches + 5 * h.it;
+    // two SpMVs and ~15 vector streams per step
+    stats->bytes_moved = ((double)A->nnz * 24.0 + 15.0 * n * 8.0) * (double)h.it;
+    return GB_OK;
+}
+
 extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
                          void *stream, PcgStats *stats) {
     gb::Range range("gbpcg:pcg_solve");
@@ -982,6 +1083,9 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
                "pcg_solve: bf16-inner precisions need bf16 values (val_types)");
     GB_REQUIRE(o.precond == GB_PC_JACOBI || o.precond == GB_PC_BLOCK_JACOBI, "pcg_solve: bad precond %d",
                o.precond);
+    GB_REQUIRE(o.method == GB_CG || o.method == GB_BICGSTAB, "pcg_solve: bad method %d", o.method);
+    GB_REQUIRE(o.method != GB_BICGSTAB || (o.precision == GB_F64 && A->C == 32 && A->warp_chunk),
+               "pcg_solve: GB_BICGSTAB runs in fp64 on C = 32 layouts");
     GB_REQUIRE(o.precond != GB_PC_BLOCK_JACOBI || A->bj_bs > 0,
                "pcg_solve: GB_PC_BLOCK_JACOBI without block-Jacobi data (sell_block_jacobi)");
     GB_REQUIRE(o.precond != GB_PC_BLOCK_JACOBI || o.precision == GB_F64 || o.precision == GB_F32_IR ||
@@ -1008,7 +1112,8 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
     ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, d_b, w.b);
     ::gb::count_launches(1); k_gather_d<<<g.vec, NT, 0, st>>>(n, A->perm, o.x0_zero ? nullptr : d_x, w.x);
     int rc;
-    if (o.precision == GB_F64) rc = solve_f64(A, o, w, st, stats);
+    if (o.method == GB_BICGSTAB) rc = solve_bicgstab(A, o, w, st, stats);
+    else if (o.precision == GB_F64) rc = solve_f64(A, o, w, st, stats);
     else if (o.precision == GB_F32_IR) rc = solve_ir<float>(A, A->val32, o, w, st, stats);
     else if (o.precision == GB_BF16_IR) rc = solve_ir<__nv_bfloat16>(A, A->val16, o, w, st, stats);
     else if (o.precision == GB_F32_RU) rc = solve_ru<float>(A, A->val32, o, w, st, stats);
@@ -1324,6 +1429,7 @@ extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_
     PcgOptions o = defaults(opt, A->n);
     GB_REQUIRE(o.precision == GB_F64, "pcg_solve_noalloc: only precision GB_F64 is available");
     GB_REQUIRE(o.precond == GB_PC_JACOBI, "pcg_solve_noalloc: the Jacobi preconditioner only");
+    GB_REQUIRE(o.method == GB_CG, "pcg_solve_noalloc: CG only");
     o.use_graph = 0;  // graph objects would allocate: the loop is polled direct launches
     const int64_t n = A->n;
     const Grids g = pick_grids(n, A->C);

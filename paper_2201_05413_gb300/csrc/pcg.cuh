@@ -27,6 +27,9 @@ struct PcgScal {
     int use_cond;
     int check_p;          // the p update makes this iteration's Eq. (2) test
     cudaGraphConditionalHandle cond;
+    double omega, rho0;   // BiCGSTAB: omega, the previous rho
+    int early;            // BiCGSTAB: the step stopped on ||s|| (x += alpha ph only)
+    int brk;              // BiCGSTAB: which quantity broke down (1 r^.v, 2 t.t, 3 ||s||, 4 rho, 5 omega)
 };
 enum { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3, ST_TIMEOUT = 4 };
 

@@ -310,10 +310,13 @@ __device__ __forceinline__ void bulk_g2s_pol(void *dst, const void *src, uint32_
 #endif
 }
 
-template <class TV, class TX>
+// DM (dot mode): 0 returns sum_r p_r q_r (CG's p.Ap); 1 returns sum_r d1_r q_r;
+// 2 also adds sum_r q_r q_r into *dot2 (BiCGSTAB's r^.v, and t.s with t.t).
+template <class TV, class TX, int DM = 0>
 __device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__restrict__ val,
                                                 const TX *__restrict__ p, TX *__restrict__ q, int c0, int c1,
-                                                Tma2Ring<TV> &sm, uint64_t *bars, bool *timed_out) {
+                                                Tma2Ring<TV> &sm, uint64_t *bars, bool *timed_out,
+                                                const TX *__restrict__ d1 = nullptr, TX *dot2 = nullptr) {
     constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -356,7 +359,8 @@ __device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__r
             r += 32;
             if (left == 0 && cb + ci < c1 && r < A.n) q[r] = TX(0);  // an all-empty chunk
         } while (left == 0 && cb + ci < c1);
-        pr = (cb + ci < c1 && r < A.n) ? __ldg(p + r) : TX(0);
+        if constexpr (DM == 0) pr = (cb + ci < c1 && r < A.n) ? __ldg(p + r) : TX(0);
+        else pr = (cb + ci < c1 && r < A.n) ? __ldg(d1 + r) : TX(0);
     };
     next_chunk();
     TX acc = TX(0);
@@ -366,6 +370,7 @@ __device__ __forceinline__ TX spmv_warp_stream2(const SellView &A, const TV *__r
             if (r < A.n) {
                 q[r] = acc;
                 dot += pr * acc;
+                if constexpr (DM == 2) *dot2 += acc * acc;
             }
             acc = TX(0);
             next_chunk();

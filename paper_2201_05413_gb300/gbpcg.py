@@ -20,6 +20,7 @@ GB_VAL_F64, GB_VAL_F32, GB_VAL_BF16, GB_IDX16 = 1, 2, 4, 8
 GB_F64, GB_F32_IR, GB_BF16_IR, GB_F32_RU, GB_BF16_RU = 0, 1, 2, 3, 4
 GB_PC_JACOBI, GB_PC_BLOCK_JACOBI = 0, 1
 GB_KT_BLOCK_JACOBI = 256
+GB_CG, GB_BICGSTAB = 0, 1
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "NOT_CONVERGED",
                 -5: "BREAKDOWN", -6: "TIMEOUT", -7: "TOO_LARGE", 1: "PENDING"}
 
@@ -64,7 +65,7 @@ class PcgOptions(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("precision", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("check_every", C.c_int32),
                 ("use_graph", C.c_int32), ("x0_zero", C.c_int32), ("spmv_variant", C.c_int32),
-                ("persist_off", C.c_int32), ("precond", C.c_int32)]
+                ("persist_off", C.c_int32), ("precond", C.c_int32), ("method", C.c_int32)]
 
 
 class PcgStats(C.Structure):
