@@ -612,7 +612,8 @@ def run_sweep_precond():
     """Jacobi against block-Jacobi (blocks of 1..32 consecutive free dofs) on
     the sweep systems at Eq. (2)'s 1e-10: iterations, solve time (block setup
     excluded, reported apart), x/r-update kernel time, fp64 and fp32-inner
-    refinement; x_err (Eq. 1) as in the eps sweep."""
+    refinement; BiCGSTAB (fp64) with Jacobi and blocks of 2 and 4; x_err
+    (Eq. 1) as in the eps sweep."""
     import torch
     import paper_2201_05413_gb300 as P
     P.load()
@@ -643,6 +644,14 @@ def run_sweep_precond():
                            "solve_ms": round(st["solve_ms"], 2), "update_us": round(1e3 * ms[1], 2),
                            "iter_us": round(1e3 * sum(ms), 2),
                            "x_err": float((x - ref).norm() / ref.norm())}
+            if bs in (0, 2, 4):  # BiCGSTAB, the paper's Krylov method, with the same preconditioner
+                kb = dict(kw, method=P.GB_BICGSTAB)
+                A.solve(b, tol=TOL, max_iter=2000000, raise_on_fail=False, **kb)  # warm
+                x, st = A.solve(b, tol=TOL, max_iter=2000000, raise_on_fail=False, **kb)
+                torch.cuda.synchronize()
+                row["bicgstab_f64"] = {"status": st["status"], "steps": st["iterations"], "restarts": st["restarts"],
+                                       "relres": st["relres"], "solve_ms": round(st["solve_ms"], 2),
+                                       "x_err": float((x - ref).norm() / ref.norm())}
             print(json.dumps(row), flush=True)
         del A, d
         torch.cuda.empty_cache()
