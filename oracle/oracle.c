@@ -49,6 +49,7 @@ struct orc_sys {
     int64_t nv, ndof, nel;
     int nvert_el;   /* dim+1 */
     int nloc;       /* dofs per element */
+    int beta[35][4]; /* degree >= 3: local dof l = Lagrange node sum_a beta[l][a] P_a / degree */
     double *vx;     /* nv*dim */
     double *dx;     /* ndof*dim */
     int32_t *elv;   /* nel*nvert_el vertex ids */
@@ -88,7 +89,8 @@ static const int EDGES3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}}
 static const int KUHN[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
 orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uint64_t seed) {
-    if ((dim != 2 && dim != 3) || (degree != 1 && degree != 2) || cells < 1) return NULL;
+    if ((dim != 2 && dim != 3) || degree < 1 || degree > 4 || cells < 1) return NULL;
+    if (degree >= 3 && jitter) return NULL; /* P3/P4 on unjittered meshes only */
     orc_sys *s = (orc_sys *)calloc(1, sizeof(orc_sys));
     s->dim = dim; s->degree = degree; s->cells = cells; s->jitter = jitter;
     s->diag_mode = diag_mode; s->seed = seed;
@@ -98,6 +100,25 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
     for (int d = 0; d < dim; ++d) { s->nv *= s->V; s->ndof *= s->S; }
     s->nvert_el = dim + 1;
     s->nloc = degree == 1 ? dim + 1 : (dim == 2 ? 6 : 10);
+    if (degree >= 3) {
+        /* Lagrange nodes of degree m: multi-indices beta in N^(d+1), |beta| = m,
+         * enumerated with beta_1 slowest ... beta_d fastest, beta_0 = m - rest */
+        int l = 0;
+        if (dim == 2) {
+            for (int b1 = 0; b1 <= degree; ++b1)
+                for (int b2 = 0; b1 + b2 <= degree; ++b2, ++l) {
+                    s->beta[l][0] = degree - b1 - b2; s->beta[l][1] = b1; s->beta[l][2] = b2; s->beta[l][3] = 0;
+                }
+        } else {
+            for (int b1 = 0; b1 <= degree; ++b1)
+                for (int b2 = 0; b1 + b2 <= degree; ++b2)
+                    for (int b3 = 0; b1 + b2 + b3 <= degree; ++b3, ++l) {
+                        s->beta[l][0] = degree - b1 - b2 - b3;
+                        s->beta[l][1] = b1; s->beta[l][2] = b2; s->beta[l][3] = b3;
+                    }
+        }
+        s->nloc = l; /* (m+1)(m+2)/2 in 2D, (m+1)(m+2)(m+3)/6 in 3D */
+    }
     int64_t ncell = 1;
     for (int d = 0; d < dim; ++d) ncell *= cells;
     s->nel = ncell * (dim == 2 ? 2 : 6);
@@ -181,6 +202,24 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
             s->eld[e * s->nloc + a] = (int32_t)id;
             const int32_t v = s->elv[e * s->nvert_el + a];
             for (int d = 0; d < dim; ++d) s->dx[id * dim + d] = s->vx[(int64_t)v * dim + d];
+        }
+        if (degree >= 3) {
+            /* node beta sits at dof-lattice point sum_a beta_a v_a (vertex v_a in
+             * cell units): the degree-refined lattice; coordinates N / (degree cells) */
+            int vc[4][3];
+            for (int a = 0; a < s->nvert_el; ++a)
+                for (int d = 0; d < dim; ++d) vc[a][d] = lat[a][d] / degree;
+            for (int l = 0; l < s->nloc; ++l) {
+                int64_t id = 0, mul = 1;
+                int N[3] = {0, 0, 0};
+                for (int d = 0; d < dim; ++d) {
+                    for (int a = 0; a < s->nvert_el; ++a) N[d] += s->beta[l][a] * vc[a][d];
+                    id += N[d] * mul;
+                    mul *= s->S;
+                }
+                s->eld[e * s->nloc + l] = (int32_t)id;
+                for (int d = 0; d < dim; ++d) s->dx[id * dim + d] = (double)N[d] / (double)(s->S - 1);
+            }
         }
         if (degree == 2) {
             const int ne = dim == 2 ? 3 : 6;
@@ -298,6 +337,84 @@ static void p2_grad_coeffs(int dim, int i, double C[4][4]) {
     }
 }
 
+/* Degree m >= 3: Silvester's form of the Lagrange basis,
+ *   phi_beta(lambda) = prod_a P_{beta_a}(lambda_a),  P_k(t) = prod_{j<k} (m t - j)/(j + 1),
+ * and grad phi = sum_a (d phi / d lambda_a) grad lambda_a, so
+ *   K_{beta,gamma} = sum_{a,b} (g_a . g_b) int_T (d_a phi_beta)(d_b phi_gamma)
+ * with every integrand a product over c of polynomials in lambda_c alone,
+ * integrated monomial by monomial: int_T prod lambda_c^e_c = |T| d! prod e_c! / (d + sum e)!.
+ * The reference integrals (per unit |T|) depend on (d, m) only: tabulated once. */
+#define PMAX 4
+static int ref_dim = 0, ref_deg = 0, ref_nloc = 0;
+static double *ref_tab = NULL; /* [i][j][a][b] */
+
+/* coefficients (degree <= PMAX) of P_k and its derivative */
+static void silvester(int m, int k, double *c, double *dc) {
+    for (int i = 0; i <= PMAX; ++i) c[i] = 0.0;
+    c[0] = 1.0;
+    for (int j = 0; j < k; ++j) { /* multiply by (m t - j)/(j+1) */
+        double nc[PMAX + 1] = {0};
+        for (int i = 0; i <= PMAX; ++i) {
+            if (c[i] == 0.0) continue;
+            if (i + 1 <= PMAX) nc[i + 1] += c[i] * (double)m / (double)(j + 1);
+            nc[i] -= c[i] * (double)j / (double)(j + 1);
+        }
+        for (int i = 0; i <= PMAX; ++i) c[i] = nc[i];
+    }
+    for (int i = 0; i <= PMAX; ++i) dc[i] = (i + 1 <= PMAX) ? (double)(i + 1) * c[i + 1] : 0.0;
+}
+
+static double factorial(int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; }
+
+static void build_ref_table(const orc_sys *s) {
+    const int d = s->dim, nv = d + 1, m = s->degree, nl = s->nloc;
+    if (ref_tab && ref_dim == d && ref_deg == m) return;
+    free(ref_tab);
+    ref_tab = (double *)calloc((size_t)nl * nl * nv * nv, sizeof(double));
+    ref_dim = d; ref_deg = m; ref_nloc = nl;
+    double P[PMAX + 1][PMAX + 1], dP[PMAX + 1][PMAX + 1];
+    for (int k = 0; k <= m; ++k) silvester(m, k, P[k], dP[k]);
+    for (int i = 0; i < nl; ++i)
+        for (int j = 0; j < nl; ++j)
+            for (int a = 0; a < nv; ++a)
+                for (int b = 0; b < nv; ++b) {
+                    /* u_c = f_c h_c, f_c = (c == a ? P' : P)_{beta_i c}, h_c likewise for j, b */
+                    double u[4][2 * PMAX + 1];
+                    for (int c = 0; c < nv; ++c) {
+                        const double *f = (c == a) ? dP[s->beta[i][c]] : P[s->beta[i][c]];
+                        const double *h = (c == b) ? dP[s->beta[j][c]] : P[s->beta[j][c]];
+                        for (int t = 0; t <= 2 * PMAX; ++t) u[c][t] = 0.0;
+                        for (int p = 0; p <= PMAX; ++p)
+                            for (int q = 0; q <= PMAX; ++q) u[c][p + q] += f[p] * h[q];
+                    }
+                    /* sum over exponent tuples, each e_c up to the degree of u_c */
+                    int E[4] = {1, 1, 1, 1};
+                    for (int c = 0; c < nv; ++c) {
+                        int top = 0;
+                        for (int t = 0; t <= 2 * PMAX; ++t) if (u[c][t] != 0.0) top = t;
+                        E[c] = top + 1;
+                    }
+                    double tot = 0.0;
+                    int e[4] = {0, 0, 0, 0};
+                    int64_t ncomb = 1;
+                    for (int c = 0; c < nv; ++c) ncomb *= E[c];
+                    for (int64_t z = 0; z < ncomb; ++z) {
+                        int64_t t = z;
+                        double coef = 1.0, pf = 1.0;
+                        int se = 0;
+                        for (int c = 0; c < nv; ++c) {
+                            e[c] = (int)(t % E[c]); t /= E[c];
+                            coef *= u[c][e[c]];
+                            pf *= factorial(e[c]);
+                            se += e[c];
+                        }
+                        if (coef == 0.0) continue;
+                        tot += coef * factorial(d) * pf / factorial(d + se);
+                    }
+                    ref_tab[(((size_t)i * nl + j) * nv + a) * nv + b] = tot;
+                }
+}
+
 void orc_element_matrix(const orc_sys *s, int64_t e, double *out) {
     const int dim = s->dim, nv = dim + 1, nloc = s->nloc;
     double P[4][3] = {{0}}, g[4][3] = {{0}};
@@ -317,6 +434,18 @@ void orc_element_matrix(const orc_sys *s, int64_t e, double *out) {
         /* K_ab = |T| grad(lambda_a).grad(lambda_b) */
         for (int a = 0; a < nv; ++a)
             for (int b = 0; b < nv; ++b) out[a * nloc + b] = vol * G[a][b];
+        return;
+    }
+    if (s->degree >= 3) {
+        build_ref_table(s);
+        for (int i = 0; i < nloc; ++i)
+            for (int j = i; j < nloc; ++j) { /* K_ji = K_ij: computed once */
+                double t = 0.0;
+                for (int a = 0; a < nv; ++a)
+                    for (int b = 0; b < nv; ++b) t += G[a][b] * ref_tab[(((size_t)i * nloc + j) * nv + a) * nv + b];
+                out[i * nloc + j] = vol * t;
+                out[j * nloc + i] = vol * t;
+            }
         return;
     }
     /* int_T lambda_m lambda_n = |T| d! (1 + delta_mn) / (d+2)! */
@@ -375,7 +504,7 @@ int orc_assemble(orc_sys *s, const uint8_t *row_mask) {
     int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (s->ndof ? s->ndof : 1));
     memcpy(pos, cnt, sizeof(int64_t) * s->ndof);
     /* pass 2: scatter element matrices in element order */
-    double Ke[100];
+    double Ke[35 * 35];
     for (int64_t e = 0; e < s->nel; ++e) {
         int any = !row_mask;
         for (int a = 0; a < nloc && !any; ++a) any = row_mask[s->eld[e * nloc + a]] != 0;

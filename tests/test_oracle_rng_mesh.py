@@ -130,4 +130,6 @@ def test_bad_specs_rejected():
     with pytest.raises(ValueError):
         O.System(4, 1, 4)
     with pytest.raises(ValueError):
-        O.System(2, 3, 4)
+        O.System(2, 5, 4)  # degrees 1..4
+    with pytest.raises(ValueError):
+        O.System(2, 3, 4, jitter=1)  # P3/P4 on unjittered meshes only
