@@ -66,9 +66,9 @@ def parse():
     ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
                     help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--sweep", default=None, choices=["eps", "rhs", "precond"],
+    ap.add_argument("--sweep", default=None, choices=["eps", "rhs", "precond", "degree"],
                     help="accuracy vs stopping tolerance (eps), solve time vs number of right-hand sides (rhs), "
-                         "or Jacobi vs block-Jacobi block sizes (precond)")
+                         "Jacobi vs block-Jacobi block sizes (precond), or P1-P4 (degree)")
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-bj", type=int, default=0, metavar="BS",
                     help="profiling driver: time the block-Jacobi iteration with blocks of BS rows")
@@ -657,6 +657,50 @@ def run_sweep_precond():
         torch.cuda.empty_cache()
 
 
+def run_sweep_degree():
+    """Table 7's degree study on our meshes: P1-P4 on one unjittered mesh per
+    dimension (2D 128^2 cells with random diagonals, g = sin(pi x) sinh(pi y) /
+    sinh(pi); 3D Kuhn 16^3 with the quartic harmonic Re (x+iy)^4, reproduced
+    exactly by P4 only), solved to 1e-12 (the paper's epsilon for Table 7):
+    size, nnz per row, CG iterations and time (Jacobi, block-Jacobi bs 4),
+    BiCGSTAB with block-Jacobi (the paper's solver), and the nodal error
+    against the exact harmonic solution."""
+    import numpy as np
+    import torch
+    import paper_2201_05413_gb300 as P
+    P.load()
+    tol = 1e-12
+    for dim, cells, dm, gid, coef in ((2, 128, 1, 0, None), (3, 16, 0, 4, "re4")):
+        for deg in (1, 2, 3, 4):
+            spec = (dim, deg, cells, 0, dm, 1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d = P.FemSystem(*spec)
+            A = d.to_sell(32, 256)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            c = None
+            if coef == "re4":
+                c = np.zeros((1, 10))
+                c[0, 8] = 1.0
+            b = d.lift(d.dirichlet(gid, c))[:, 0]
+            exact = d.dirichlet(gid, c, which="free")[:, 0]
+            row = {"sweep": "degree", "dim": dim, "cells": cells, "degree": deg, "n": A.n, "nnz": A.nnz,
+                   "nnz_per_row": round(A.nnz / A.n, 2), "setup_ms": round(1e3 * t_setup, 1)}
+            A.block_jacobi(4)
+            for name, kw in (("cg", {}), ("cg_bj4", {"precond": P.GB_PC_BLOCK_JACOBI}),
+                             ("bicgstab_bj4", {"method": P.GB_BICGSTAB, "precond": P.GB_PC_BLOCK_JACOBI})):
+                A.solve(b, tol=tol, max_iter=2000000, raise_on_fail=False, **kw)  # warm
+                x, st = A.solve(b, tol=tol, max_iter=2000000, raise_on_fail=False, **kw)
+                torch.cuda.synchronize()
+                row[name] = {"status": st["status"], "iterations": st["iterations"], "solve_ms": round(st["solve_ms"], 2),
+                             "relres": st["relres"],
+                             "nodal_err": float((x - exact).abs().max() / exact.abs().max())}
+            print(json.dumps(row), flush=True)
+            del A, d
+            torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.profile_kernels:
@@ -670,6 +714,9 @@ def main():
         return
     if args.sweep == "precond":
         run_sweep_precond()
+        return
+    if args.sweep == "degree":
+        run_sweep_degree()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1,5 +1,6 @@
 // fem.cu -- device mesh, dof numbering, stiffness assembly, Dirichlet data
-// and lift (paper Sec. 2.2; P2 as in the degree study of Sec. 4.2).
+// and lift (paper Sec. 2.2; P2-P4 as in the degree study of Sec. 4.2, P3/P4
+// on unjittered meshes).
 //
 // The mesh is implicit: a vertex's coordinates and a cell's diagonal are pure
 // functions of the lattice index and the counter-based generator, so nothing
@@ -11,6 +12,8 @@
 // entries are evaluated for the ordered local pair (min, max), so K_ij and
 // K_ji are the same sum of the same terms in the same order: K_II is
 // bit-exactly symmetric and the assembly is deterministic without atomics.
+#include <vector>
+
 #include "common.cuh"
 
 namespace gb {
@@ -34,6 +37,7 @@ struct MeshDev {
     int dim, deg, cells, S, V, jitter, diag_mode;
     uint64_t kx, ky, kz, kf;
     double q;  // jitter amplitude: h/4 in 2D, h/8 in 3D
+    const double *ref;  // degree >= 3: reference gradient integrals [lo][hi][a][b] per unit volume
 };
 
 // 2D triangles of a cell as vertex offsets (dx, dy): [flip][tri][vertex].
@@ -133,9 +137,38 @@ __device__ __forceinline__ void cell_element(const MeshDev &m, const int *cell, 
     }
 }
 
-// dof-lattice point of local dof `l` (vertices first, then edge midpoints)
+// Degree >= 3: local dof l is the Lagrange node with barycentric multi-index
+// beta (|beta| = DEG), taken in the order beta_0 = DEG, DEG-1, ..., 0 (outer),
+// then beta_1 likewise, ... (beta_DIM = the rest).
+template <int DIM, int DEG>
+__host__ __device__ __forceinline__ void node_beta(int l, int *beta) {
+    int k = 0;
+    for (int b0 = DEG; b0 >= 0; --b0) {
+        if (DIM == 2) {
+            for (int b1 = DEG - b0; b1 >= 0; --b1, ++k)
+                if (k == l) { beta[0] = b0; beta[1] = b1; beta[2] = DEG - b0 - b1; return; }
+        } else {
+            for (int b1 = DEG - b0; b1 >= 0; --b1)
+                for (int b2 = DEG - b0 - b1; b2 >= 0; --b2, ++k)
+                    if (k == l) { beta[0] = b0; beta[1] = b1; beta[2] = b2; beta[3] = DEG - b0 - b1 - b2; return; }
+        }
+    }
+}
+
+// dof-lattice point of local dof `l` (P1/P2: vertices first, then edge
+// midpoints; degree >= 3: the node sum_a beta_a v_a of the refined lattice)
 template <int DIM, int DEG>
 __device__ __forceinline__ void local_dof(const Elem<DIM> &e, int l, int *N) {
+    if (DEG >= 3) {
+        int beta[4] = {0, 0, 0, 0};
+        node_beta<DIM, DEG>(l, beta);
+        for (int d = 0; d < DIM; ++d) {
+            int t = 0;
+            for (int a = 0; a <= DIM; ++a) t += beta[a] * e.v[a][d];
+            N[d] = t;
+        }
+        return;
+    }
     if (l <= DIM) {
         for (int d = 0; d < DIM; ++d) N[d] = DEG * e.v[l][d];
     } else {
@@ -197,8 +230,17 @@ __device__ __forceinline__ double simplex_geometry(const MeshDev &m, const Elem<
 //   edge (a,b) - edge (c,e): 16c|T| ((1+d_ac) G_be + (1+d_ae) G_bc + (1+d_bc) G_ae + (1+d_be) G_ac)
 // with c = d!/(d+2)! (1/12 in 2D, 1/20 in 3D).
 template <int DIM, int DEG>
-__device__ __forceinline__ double entry(int lo, int hi, double vol, const double G[DIM + 1][DIM + 1]) {
+__device__ __forceinline__ double entry(int lo, int hi, double vol, const double G[DIM + 1][DIM + 1],
+                                        const double *ref) {
     if (DEG == 1) return vol * G[lo][hi];
+    if (DEG >= 3) {  // |T| sum_ab G_ab I[lo][hi][a][b], the table built on the host
+        constexpr int NL = DIM == 2 ? (DEG + 1) * (DEG + 2) / 2 : (DEG + 1) * (DEG + 2) * (DEG + 3) / 6;
+        const double *I = ref + ((size_t)lo * NL + hi) * (DIM + 1) * (DIM + 1);
+        double t = 0.0;
+        for (int a = 0; a <= DIM; ++a)
+            for (int b = 0; b <= DIM; ++b) t += G[a][b] * __ldg(I + a * (DIM + 1) + b);
+        return vol * t;
+    }
     constexpr double c = DIM == 2 ? 1.0 / 12.0 : 1.0 / 20.0;
     constexpr double inv_d1 = 1.0 / (DIM + 1);
     if (hi <= DIM) {  // both vertices
@@ -229,7 +271,9 @@ struct RowCfg {
     static constexpr int W = 2 * DEG + 1;
     static constexpr int NS = DIM == 2 ? W * W : W * W * W;
     static constexpr int NW = (NS + 31) / 32;
-    static constexpr int NLOC = DEG == 1 ? DIM + 1 : (DIM == 2 ? 6 : 10);
+    static constexpr int NLOC = DEG == 1   ? DIM + 1
+                                : DIM == 2 ? (DEG + 1) * (DEG + 2) / 2
+                                           : (DEG + 1) * (DEG + 2) * (DEG + 3) / 6;
     static constexpr int NEL = DIM == 2 ? 2 : 6;
 };
 
@@ -266,7 +310,7 @@ __device__ __forceinline__ void gather_row(const MeshDev &m, const int *I, doubl
                         int s = 0, mul = 1;
                         for (int d = 0; d < DIM; ++d) { s += (N[l][d] - I[d] + DEG) * mul; mul *= R::W; }
                         mark[s >> 5] |= 1u << (s & 31);
-                        if (WANT_VAL) acc[s] += entry<DIM, DEG>(min(li, l), max(li, l), vol, G);
+                        if (WANT_VAL) acc[s] += entry<DIM, DEG>(min(li, l), max(li, l), vol, G, m.ref);
                     }
                 }
 }
@@ -340,6 +384,10 @@ __global__ void __launch_bounds__(128) k_fill_rows(MeshDev m, int64_t n_free, co
 // whose endpoints round the odd coordinates down/up (in 2D, a cell-centre
 // point lies on the cell's diagonal, whose direction depends on the flip).
 __device__ void dof_coords(const MeshDev &m, const int *N, double *x) {
+    if (m.deg >= 3) {  // unjittered meshes only: the refined lattice point N / (deg cells)
+        for (int d = 0; d < m.dim; ++d) x[d] = __ddiv_rn((double)N[d], (double)(m.S - 1));
+        return;
+    }
     if (m.deg == 1) {
         for (int d = 0; d < m.dim; ++d) x[d] = vertex_coord(m, N, d);
         return;
@@ -460,14 +508,80 @@ struct gb_fem_system {
     int32_t *rp = nullptr, *col = nullptr, *rp_ib = nullptr, *col_ib = nullptr;
     double *val = nullptr, *val_ib = nullptr, *diag = nullptr;
     int32_t *full_of_bnd = nullptr;
+    double *ref = nullptr;  // degree >= 3: reference integrals on the device
 };
 
 using namespace gb;
+
+// Reference integrals of the degree-m (m >= 3) Lagrange basis on a d-simplex,
+// per unit volume: I[l][k][a][b] = (1/|T|) int_T (d phi_l/d lambda_a)(d phi_k/d lambda_b),
+// phi_beta = prod_c s_{beta_c}(lambda_c) with s_j(t) = prod_{i<j} (m t - i)/(i + 1).
+// Each integrand is a product of one polynomial per lambda_c; with
+// int_T prod lambda_c^e_c = |T| d! prod e_c! / (d + sum e_c)!, the integral is
+// d! sum_E W[E] / (d + E)!, W the convolution over c of w_c[e] = coef_c[e] e!.
+template <int DIM, int DEG>
+static std::vector<double> reference_table() {
+    constexpr int NL = RowCfg<DIM, DEG>::NLOC, NV = DIM + 1, PD = 2 * DEG;
+    double sj[DEG + 1][DEG + 1] = {}, dsj[DEG + 1][DEG + 1] = {};  // coefficients by power
+    for (int j = 0; j <= DEG; ++j) {
+        double c[DEG + 1] = {};
+        c[0] = 1.0;
+        for (int i = 0; i < j; ++i) {  // times (m t - i)/(i + 1)
+            double nc[DEG + 1] = {};
+            for (int p = 0; p <= DEG; ++p) {
+                if (p + 1 <= DEG) nc[p + 1] += c[p] * DEG / (i + 1.0);
+                nc[p] -= c[p] * i / (i + 1.0);
+            }
+            for (int p = 0; p <= DEG; ++p) c[p] = nc[p];
+        }
+        for (int p = 0; p <= DEG; ++p) {
+            sj[j][p] = c[p];
+            dsj[j][p] = p + 1 <= DEG ? (p + 1) * c[p + 1] : 0.0;
+        }
+    }
+    double fact[NV * PD + NV + 1];
+    fact[0] = 1.0;
+    for (int i = 1; i <= NV * PD + NV; ++i) fact[i] = fact[i - 1] * i;
+    std::vector<double> I((size_t)NL * NL * NV * NV, 0.0);
+    for (int l = 0; l < NL; ++l)
+        for (int k = 0; k < NL; ++k) {
+            int bl[4] = {0, 0, 0, 0}, bk[4] = {0, 0, 0, 0};
+            node_beta<DIM, DEG>(l, bl);
+            node_beta<DIM, DEG>(k, bk);
+            for (int a = 0; a < NV; ++a)
+                for (int b = 0; b < NV; ++b) {
+                    std::vector<double> W(1, 1.0);  // running convolution
+                    for (int c = 0; c < NV; ++c) {
+                        const double *f = c == a ? dsj[bl[c]] : sj[bl[c]];
+                        const double *h = c == b ? dsj[bk[c]] : sj[bk[c]];
+                        double w[PD + 1] = {};
+                        for (int p = 0; p <= DEG; ++p)
+                            for (int q = 0; q <= DEG; ++q) w[p + q] += f[p] * h[q];
+                        for (int e = 0; e <= PD; ++e) w[e] *= fact[e];
+                        std::vector<double> nW(W.size() + PD, 0.0);
+                        for (size_t x = 0; x < W.size(); ++x)
+                            for (int e = 0; e <= PD; ++e) nW[x + e] += W[x] * w[e];
+                        W.swap(nW);
+                    }
+                    double t = 0.0;
+                    for (size_t E = 0; E < W.size(); ++E) t += W[E] * fact[DIM] / fact[DIM + E];
+                    I[(((size_t)l * NL + k) * NV + a) * NV + b] = t;
+                }
+        }
+    return I;
+}
 
 template <int DIM, int DEG>
 static int assemble_impl(gb_fem_system *s, cudaStream_t st) {
     Mem &mem = s->mem;
     const int64_t n = s->n_free;
+    if (DEG >= 3) {
+        const std::vector<double> I = reference_table<DIM, DEG>();
+        GB_TRY(mem.alloc_n(&s->ref, I.size()));
+        GB_CHECK_CUDA(cudaMemcpyAsync(s->ref, I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));  // I is freed on return
+        s->m.ref = s->ref;
+    }
     int32_t *len = nullptr, *len_ib = nullptr;
     int *d_max = nullptr;
     struct Temps {  // the row-length temporaries go back on every return path
@@ -520,7 +634,8 @@ extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, 
     GB_REQUIRE(spec && out, "fem_assemble: NULL argument");
     *out = nullptr;
     GB_REQUIRE(spec->dim == 2 || spec->dim == 3, "fem_assemble: dim must be 2 or 3");
-    GB_REQUIRE(spec->degree == 1 || spec->degree == 2, "fem_assemble: degree must be 1 or 2");
+    GB_REQUIRE(spec->degree >= 1 && spec->degree <= 4, "fem_assemble: degree must be 1, 2, 3 or 4");
+    GB_REQUIRE(spec->degree <= 2 || spec->jitter == 0, "fem_assemble: P3/P4 on unjittered meshes only");
     GB_REQUIRE(spec->cells >= 2, "fem_assemble: cells must be >= 2");
     GB_REQUIRE(spec->jitter == 0 || spec->jitter == 1, "fem_assemble: jitter must be 0 or 1");
     GB_REQUIRE(spec->diag_mode == 0 || spec->diag_mode == 1, "fem_assemble: diag_mode must be 0 or 1");
@@ -545,9 +660,18 @@ extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, 
     m.kz = stream_key(spec->seed, 3);
     m.q = (spec->dim == 3 ? 0.125 : 0.25) / (double)spec->cells;
     s->n_dof = n_dof; s->n_free = n_free; s->n_bnd = n_dof - n_free;
+    m.ref = nullptr;
     int rc;
-    if (m.dim == 2) rc = m.deg == 1 ? assemble_impl<2, 1>(s, st) : assemble_impl<2, 2>(s, st);
-    else rc = m.deg == 1 ? assemble_impl<3, 1>(s, st) : assemble_impl<3, 2>(s, st);
+    switch (m.dim * 10 + m.deg) {
+    case 21: rc = assemble_impl<2, 1>(s, st); break;
+    case 22: rc = assemble_impl<2, 2>(s, st); break;
+    case 23: rc = assemble_impl<2, 3>(s, st); break;
+    case 24: rc = assemble_impl<2, 4>(s, st); break;
+    case 31: rc = assemble_impl<3, 1>(s, st); break;
+    case 32: rc = assemble_impl<3, 2>(s, st); break;
+    case 33: rc = assemble_impl<3, 3>(s, st); break;
+    default: rc = assemble_impl<3, 4>(s, st); break;
+    }
     if (rc != GB_OK) { fem_system_destroy(s); return rc; }
     *out = s;
     return GB_OK;
@@ -593,7 +717,7 @@ extern "C" int fem_dirichlet(const gb_fem_system *s, int gid, const double *h_co
     GB_REQUIRE(gid >= 0 && gid <= 4, "fem_dirichlet: gid must be in 0..4");
     GB_REQUIRE(k >= 1, "fem_dirichlet: k must be >= 1");
     GB_REQUIRE(which == 0 || which == 1, "fem_dirichlet: which must be 0 or 1");
-    GB_REQUIRE(s->m.dim == 2 || gid == 2 || gid == 3, "fem_dirichlet: gid %d is 2D only", gid);
+    GB_REQUIRE(s->m.dim == 2 || gid >= 2, "fem_dirichlet: gid %d is 2D only", gid);  // gid 4 (x + iy) is harmonic in 3D too
     const int nc = gid_ncoef(gid);
     GB_REQUIRE(nc == 0 || h_coef, "fem_dirichlet: gid %d needs coefficients", gid);
     cudaStream_t st = (cudaStream_t)stream;
@@ -632,6 +756,7 @@ extern "C" void fem_system_destroy(gb_fem_system *s) {
     m.release(s->rp_ib); m.release(s->col_ib); m.release(s->val_ib);
     m.release(s->diag);
     m.release(s->full_of_bnd);
+    m.release(s->ref);
     delete s;
 }
 

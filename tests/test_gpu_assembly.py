@@ -159,7 +159,7 @@ def test_bad_specs_raise(P):
     with pytest.raises(P.GbError):
         P.FemSystem(3, 1, 8, jitter=1, diag_mode=1)  # 3D: the Kuhn split only
     with pytest.raises(P.GbError):
-        P.FemSystem(2, 3, 8)
+        P.FemSystem(2, 5, 8)
     with pytest.raises(P.GbError):
         P.FemSystem(2, 1, 1)
 
