@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-bj", type=int, default=0, metavar="BS",
                     help="profiling driver: time the block-Jacobi iteration with blocks of BS rows")
+    ap.add_argument("--profile-rhs", type=int, default=0, metavar="K",
+                    help="profiling driver: time the blocked multi-RHS iteration with K harmonic right-hand sides")
     return ap.parse_args()
 
 
@@ -404,8 +406,18 @@ def run_profile(args):
     dim, deg, cells, jit, dm, seed, gid = PROFILE_SYSTEMS[args.profile_kernels]
     d = P.FemSystem(dim, deg, cells, jit, dm, seed)
     A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32 | P.GB_VAL_BF16)
-    b = d.lift(d.dirichlet(gid))[:, 0]
     prec = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR}[args.profile_precision]
+    if args.profile_rhs:
+        import numpy as np
+        k = args.profile_rhs
+        coef = np.random.default_rng(3).standard_normal((k, 10))
+        B = d.lift(d.dirichlet(4 if dim == 2 else 3, coef if dim == 2 else coef[:, :4], k))
+        ms = P.batched_kernel_times([A], [B], prec, args.profile_iters)
+        torch.cuda.synchronize()
+        print(json.dumps({"system": args.profile_kernels, "precision": args.profile_precision, "n": A.n,
+                          "nnz": A.nnz, "k": k, "kernel_ms": ms}))
+        return
+    b = d.lift(d.dirichlet(gid))[:, 0]
     if args.profile_bj:
         A.block_jacobi(args.profile_bj)
         prec |= P.gbpcg.GB_KT_BLOCK_JACOBI
