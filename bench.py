@@ -436,7 +436,8 @@ def run_multi_rhs(iters=5):
     right-hand sides from harmonic-basis coefficients N(0,1), host seed 3):
     per-kernel CUDA-event times of the batched SpMM, X/R update and P update,
     fp64 and fp32 recurrences, with the algorithmic bytes per iteration
-    (matrix once, 7 vector streams of n x k) against the HBM peak."""
+    (matrix once, 7 vector streams of n x k) against the HBM peak, and the
+    RHS block width the autotuner picks (iteration time per width)."""
     import torch
     import paper_2201_05413_gb300 as P
     from paper_2201_05413_gb300.workloads import multi_rhs_coefficients
@@ -457,6 +458,10 @@ def run_multi_rhs(iters=5):
                    "algorithmic_GBps": round(algo / (it_ms * 1e-3) / 1e9, 1),
                    "frac_of_hbm_peak": round(algo / (it_ms * 1e-3) / 1e9 / peak, 4),
                    "GFLOPps": round(flops / (it_ms * 1e-3) / 1e9, 1)}
+        # RHS block width autotuner: iteration time of the 32 columns cut into groups of w
+        w, wms = P.autotune_rhs_width(A, B, precision=pv)
+        out[pn]["autotuned_width"] = w
+        out[pn]["iter_ms_by_width"] = {str(c): round(t, 4) for c, t in wms.items()}
     out["peak_source"] = src
     del B, A, d
     torch.cuda.empty_cache()

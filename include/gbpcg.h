@@ -438,6 +438,16 @@ int pcg_kernel_times(const gb_sell *A, const double *d_b, int precision, int ite
 int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const double *const *d_B, const int *k,
                              int precision, int iters, void *stream, double *h_ms);
 
+/* RHS block width autotuner for blocked multi-RHS solves: the k columns of
+ * d_B (n x k row-major, original order, 1 <= k <= 256) are cut into groups of
+ * w = 1, 2, 4, 8, 16, 32 columns (w <= k); for each w one blocked iteration
+ * of that batch (pcg_solve_batched's kernels) is timed with CUDA events and
+ * *best_width receives the width with the least time; h_ms (6 doubles, may be
+ * NULL) the iteration time per width (0 where w > k).  Pass groups of
+ * *best_width columns to pcg_solve_batched.  Synchronises `stream`. */
+int pcg_batched_autotune_width(const gb_sell *A, const double *d_B, int k, int precision, void *stream,
+                               int *best_width, double *h_ms);
+
 /* Diagnostic entry point (no counterpart in the paper): exercises, on the
  * GPU, the bounded wait that the library's kernels use on their shared-memory
  * transaction barriers.  One warp arms a barrier that nothing completes and

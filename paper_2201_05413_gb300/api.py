@@ -294,6 +294,28 @@ def batched_kernel_times(mats, Bs, precision=G.GB_F64, iters=20, stream=None):
     return list(ms)
 
 
+def autotune_rhs_width(A, B, precision=G.GB_F64, stream=None):
+    """pcg_batched_autotune_width: the RHS block width (columns per system of
+    the batch) with the fastest blocked iteration for the n x k block B;
+    returns (width, {width: iteration ms})."""
+    B = B.contiguous()
+    k = B.shape[1]
+    best = C.c_int(0)
+    ms = (C.c_double * 6)()
+    G.check(G.lib().pcg_batched_autotune_width(A.handle, G.ptr(B), k, precision, G.stream_ptr(stream),
+                                               C.byref(best), ms), "pcg_batched_autotune_width")
+    return best.value, {w: ms[i] for i, w in enumerate((1, 2, 4, 8, 16, 32)) if w <= k}
+
+
+def solve_multi(A, B, width, stream=None, **kw):
+    """pcg_solve_batched over groups of `width` columns of the n x k block B
+    (the blocked multi-RHS solve of Eq. MRH); returns (X, per-group stats)."""
+    B = B.contiguous()
+    groups = [B[:, j:j + width].contiguous() for j in range(0, B.shape[1], width)]
+    Xs, sts = pcg_solve_batched([A] * len(groups), groups, stream=stream, **kw)
+    return torch.cat(Xs, dim=1), sts
+
+
 def wait_selftest(limit_ms=20.0, stream=None):
     """gbpcg_wait_selftest: (status code, milliseconds the bounded wait waited)."""
     waited = C.c_double(0.0)

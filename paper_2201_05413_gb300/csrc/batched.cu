@@ -368,6 +368,15 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
 }
 
 // ------------------------------------------------------------ measurement --
+// out (n x w, row-major) = columns j0 .. j0+w-1 of B (n x k, row-major)
+__global__ void k_col_slice(int64_t n, int k, int j0, int w, const double *__restrict__ B, double *__restrict__ out) {
+    const int64_t m = n * w;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / w;
+        out[t] = B[r * k + j0 + (t - r * w)];
+    }
+}
+
 extern "C" int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const double *const *d_B, const int *k,
                                         int precision, int iters, void *stream, double *h_ms) {
     GB_REQUIRE(nsys >= 1 && A && d_B && k && h_ms, "pcg_batched_kernel_times: NULL argument");
@@ -451,5 +460,51 @@ extern "C" int pcg_batched_kernel_times(int nsys, const gb_sell *const *A, const
         set_error("pcg_batched_kernel_times: the recurrences stopped early; use fewer iterations");
         return GB_BREAKDOWN;
     }
+    return GB_OK;
+}
+
+// RHS block width autotuner: for each width w in {1, 2, 4, 8, 16, 32} (w <= k)
+// the k columns are cut into ceil(k/w) systems of at most w columns (the last
+// one shorter), one blocked iteration of that batch is timed with
+// pcg_batched_kernel_times (2 warm-up + 8 timed iterations), and the width
+// with the least time per column wins.
+extern "C" int pcg_batched_autotune_width(const gb_sell *A, const double *d_B, int k, int precision, void *stream,
+                                          int *best_width, double *h_ms) {
+    GB_REQUIRE(A && d_B && best_width, "pcg_batched_autotune_width: NULL argument");
+    GB_REQUIRE(k >= 1 && k <= 256, "pcg_batched_autotune_width: k=%d not in 1..256", k);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = A->n;
+    Mem mem(nullptr, st);
+    double *tmp = nullptr;
+    GB_TRY(mem.alloc_n(&tmp, (size_t)n * k));
+    struct Guard { Mem &m; double *p; ~Guard() { m.release(p); } } guard{mem, tmp};
+    double best = 1e300;
+    *best_width = 0;
+    const int widths[6] = {1, 2, 4, 8, 16, 32};
+    for (int wi = 0; wi < 6; ++wi) {
+        const int w = widths[wi];
+        if (w > k) break;
+        std::vector<const gb_sell *> As;
+        std::vector<const double *> Bs;
+        std::vector<int> ks;
+        for (int j0 = 0; j0 < k; j0 += w) {
+            const int ww = std::min(w, k - j0);
+            double *dst = tmp + (size_t)n * j0;
+            ::gb::count_launches(1);
+            k_col_slice<<<stride_grid(n * ww, 256, 8), 256, 0, st>>>(n, k, j0, ww, d_B, dst);
+            As.push_back(A);
+            Bs.push_back(dst);
+            ks.push_back(ww);
+        }
+        GB_CHECK_CUDA(cudaGetLastError());
+        double ms[3] = {0, 0, 0};
+        GB_TRY(pcg_batched_kernel_times((int)As.size(), As.data(), Bs.data(), ks.data(), precision, 2, stream, ms));
+        GB_TRY(pcg_batched_kernel_times((int)As.size(), As.data(), Bs.data(), ks.data(), precision, 8, stream, ms));
+        const double t = ms[0] + ms[1] + ms[2];
+        if (h_ms) h_ms[wi] = t;
+        if (t < best) { best = t; *best_width = w; }
+    }
+    for (int wi = 0; wi < 6 && h_ms; ++wi)
+        if (widths[wi] > k) h_ms[wi] = 0.0;
     return GB_OK;
 }
