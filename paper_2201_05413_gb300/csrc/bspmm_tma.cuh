@@ -37,10 +37,14 @@ template <class TX, int K> struct BSlice {
 #endif
 template <class TX, int K> struct BspmmOcc {
     static constexpr int ACC = K * (int)sizeof(TX) / 4;  // accumulator registers
-    // gather buffer: 16 registers; rows of 64 bytes or more (G >= 4 lanes per
-    // row) take GB_BSPMM_WIDE_GBUF when it still fits 128 registers
+    // gather buffer: 16 registers; fp32 rows of 64 bytes or more (G >= 4
+    // lanes per row) take GB_BSPMM_WIDE_GBUF when it still fits 128 registers
+    // (fp32, k = 32 on 2D P2 1024^2: 0.93 ms with 32, 1.17 ms with 24, 1.22 ms
+    // with 16); fp64 keeps 16, which leaves k = 8 three blocks per SM (0.865
+    // against 0.895 ms with 32)
     static constexpr int GBUF =
-        (K * (int)sizeof(TX) >= 64 && ACC + GB_BSPMM_WIDE_GBUF + 44 <= 128) ? GB_BSPMM_WIDE_GBUF : 16;
+        (sizeof(TX) == 4 && K * (int)sizeof(TX) >= 64 && ACC + GB_BSPMM_WIDE_GBUF + 44 <= 128) ? GB_BSPMM_WIDE_GBUF
+                                                                                              : 16;
     static constexpr int R = ACC + GBUF + 44;
     static constexpr int blocks = R <= 64 ? 4 : (R <= 84 ? 3 : 2);
 };

@@ -110,7 +110,10 @@ int num_sms();
 #endif
 constexpr int TMA_BLOCKS_PER_SM = GB_TMA_BLOCKS_PER_SM;
 // the fp32 SpMV (smaller shared-memory ring) runs 5 blocks per SM
-constexpr int TMA_BLOCKS_PER_SM_NARROW = 5;
+#ifndef GB_TMA_BLOCKS_PER_SM_NARROW
+#define GB_TMA_BLOCKS_PER_SM_NARROW 5
+#endif
+constexpr int TMA_BLOCKS_PER_SM_NARROW = GB_TMA_BLOCKS_PER_SM_NARROW;
 // Grid for a grid-stride kernel: a multiple of the SM count, at most `want`.
 inline int stride_grid(int64_t work_items, int block, int per_sm) {
     int sms = num_sms();
