@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-bj", type=int, default=0, metavar="BS",
                     help="profiling driver: time the block-Jacobi iteration with blocks of BS rows")
+    ap.add_argument("--profile-solve", default=None, choices=["bicgstab", "blockcg"],
+                    help="profiling driver: one solve of the profile system with direct launches (BiCGSTAB, or "
+                         "block CG with --profile-rhs columns)")
     ap.add_argument("--profile-rhs", type=int, default=0, metavar="K",
                     help="profiling driver: time the blocked multi-RHS iteration with K harmonic right-hand sides")
     return ap.parse_args()
@@ -407,6 +410,23 @@ def run_profile(args):
     d = P.FemSystem(dim, deg, cells, jit, dm, seed)
     A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32 | P.GB_VAL_BF16)
     prec = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR}[args.profile_precision]
+    if args.profile_solve == "bicgstab":
+        b = d.lift(d.dirichlet(gid))[:, 0]
+        x, st = A.solve(b, tol=1e-10, method=P.GB_BICGSTAB, use_graph=0, max_iter=args.profile_iters,
+                        raise_on_fail=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"system": args.profile_kernels, "solve": "bicgstab", "n": A.n, "steps": st["iterations"]}))
+        return
+    if args.profile_solve == "blockcg":
+        import numpy as np
+        k = args.profile_rhs or 8
+        coef = np.random.default_rng(3).standard_normal((k, 10))
+        B = d.lift(d.dirichlet(4, coef, k))
+        X, st = A.solve_block(B, tol=1e-10, precision=prec, max_iter=args.profile_iters, raise_on_fail=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"system": args.profile_kernels, "solve": "blockcg", "n": A.n, "k": k,
+                          "steps": st["iterations"]}))
+        return
     if args.profile_rhs:
         import numpy as np
         k = args.profile_rhs
