@@ -90,7 +90,6 @@ static const int KUHN[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0
 
 orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uint64_t seed) {
     if ((dim != 2 && dim != 3) || degree < 1 || degree > 4 || cells < 1) return NULL;
-    if (degree >= 3 && jitter) return NULL; /* P3/P4 on unjittered meshes only */
     orc_sys *s = (orc_sys *)calloc(1, sizeof(orc_sys));
     s->dim = dim; s->degree = degree; s->cells = cells; s->jitter = jitter;
     s->diag_mode = diag_mode; s->seed = seed;
@@ -205,7 +204,11 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
         }
         if (degree >= 3) {
             /* node beta sits at dof-lattice point sum_a beta_a v_a (vertex v_a in
-             * cell units): the degree-refined lattice; coordinates N / (degree cells) */
+             * cell units): the degree-refined lattice.  Its coordinates are
+             * (sum_a beta_a P_a) / degree over the vertices with beta_a > 0 -- the
+             * smallest mesh face holding the node, the same from every element
+             * around it -- summed in ascending vertex id with correctly rounded
+             * operations; a vertex node is the vertex itself. */
             int vc[4][3];
             for (int a = 0; a < s->nvert_el; ++a)
                 for (int d = 0; d < dim; ++d) vc[a][d] = lat[a][d] / degree;
@@ -218,7 +221,21 @@ orc_sys *orc_mesh(int dim, int degree, int cells, int jitter, int diag_mode, uin
                     mul *= s->S;
                 }
                 s->eld[e * s->nloc + l] = (int32_t)id;
-                for (int d = 0; d < dim; ++d) s->dx[id * dim + d] = (double)N[d] / (double)(s->S - 1);
+                int32_t fv[4];
+                int fb[4], nf = 0;
+                for (int a = 0; a < s->nvert_el; ++a)
+                    if (s->beta[l][a] > 0) { fv[nf] = s->elv[e * s->nvert_el + a]; fb[nf] = s->beta[l][a]; ++nf; }
+                for (int i = 1; i < nf; ++i) { /* ascending vertex id */
+                    int32_t tv = fv[i]; int tb = fb[i], j = i;
+                    while (j > 0 && fv[j - 1] > tv) { fv[j] = fv[j - 1]; fb[j] = fb[j - 1]; --j; }
+                    fv[j] = tv; fb[j] = tb;
+                }
+                for (int d = 0; d < dim; ++d) {
+                    if (nf == 1) { s->dx[id * dim + d] = s->vx[(int64_t)fv[0] * dim + d]; continue; }
+                    double t = 0.0;
+                    for (int i = 0; i < nf; ++i) t = t + (double)fb[i] * s->vx[(int64_t)fv[i] * dim + d];
+                    s->dx[id * dim + d] = t / (double)degree;
+                }
             }
         }
         if (degree == 2) {

@@ -1,5 +1,6 @@
 """Pins of the oracle's P3 and P4 elements (the degree study of Sec. 4.2,
-Table 7) against routes independent of its Silvester-basis table:
+Table 7), regular and jittered meshes, against routes independent of its
+Silvester-basis table:
 
 - element matrices = Lagrange bases from a Vandermonde solve at the nodes,
   integrated with a collapsed Gauss-Legendre rule;
@@ -10,7 +11,10 @@ Table 7) against routes independent of its Silvester-basis table:
 - convergence: for the smooth harmonic sin(pi x) sinh(pi y)/sinh(pi) the
   nodal error falls at least like h^m when h halves (order m+1 expected);
 - pattern = brute-force set of pairs sharing an element; counts
-  (m cells + 1)^d dofs, C(m+d, d) per element.
+  (m cells + 1)^d dofs, C(m+d, d) per element;
+- node coordinates on jittered meshes follow their definition, (sum of
+  beta_a P_a over the node's smallest face, ascending vertex id) / m, bit for
+  bit from every element around the node.
 """
 import itertools
 import math
@@ -24,7 +28,8 @@ from test_oracle_element import _quad_simplex, _monomials, _lagrange_coeffs, _gr
 
 
 def _elem_vertices(s, e, X, E):
-    """the element's vertex nodes: dof-lattice coordinates multiples of m"""
+    """the element's vertex nodes (dof-lattice coordinates multiples of m), in
+    the element's vertex order"""
     S = s.n_dof ** (1.0 / s.dim)
     S = int(round(S))
     ids = E[e]
@@ -47,9 +52,10 @@ def _stiffness_by_quadrature(nodes, P, deg):
     return K
 
 
-@pytest.mark.parametrize("dim,degree,cells", [(2, 3, 3), (2, 4, 3), (3, 3, 2), (3, 4, 2)])
-def test_element_matrix_vs_lagrange_quadrature(dim, degree, cells):
-    s = O.System(dim, degree, cells, jitter=0, diag_mode=1, seed=5)
+@pytest.mark.parametrize("dim,degree,cells,jitter", [(2, 3, 3, 0), (2, 4, 3, 0), (3, 3, 2, 0), (3, 4, 2, 0),
+                                                     (2, 3, 4, 1), (2, 4, 4, 1), (3, 3, 3, 1), (3, 4, 3, 1)])
+def test_element_matrix_vs_lagrange_quadrature(dim, degree, cells, jitter):
+    s = O.System(dim, degree, cells, jitter=jitter, diag_mode=1 if dim == 2 else 0, seed=5)
     assert s.n_loc == math.comb(degree + dim, dim)
     assert s.n_dof == (degree * cells + 1) ** dim
     X = s.dof_coords()
@@ -59,7 +65,7 @@ def test_element_matrix_vs_lagrange_quadrature(dim, degree, cells):
         P = _elem_vertices(s, e, X, E)
         Kq = _stiffness_by_quadrature(nodes, P, degree)
         Ko = s.element_matrix(e)
-        assert np.abs(Ko - Kq).max() <= 1e-10 * np.abs(Kq).max()
+        assert np.abs(Ko - Kq).max() <= 1e-9 * np.abs(Kq).max()
         assert np.array_equal(Ko, Ko.T)
         assert np.abs(Ko.sum(1)).max() <= 1e-12 * np.abs(Ko).max()
         assert np.linalg.eigvalsh(Ko).min() > -1e-12 * np.abs(Ko).max()
@@ -78,13 +84,13 @@ CUBIC = [lambda X: X[:, 0] ** 3 - 3 * X[:, 0] * X[:, 1] ** 2, lambda X: 3 * X[:,
 QUARTIC = lambda X: X[:, 0] ** 4 - 6 * X[:, 0] ** 2 * X[:, 1] ** 2 + X[:, 1] ** 4
 
 
-@pytest.mark.parametrize("dim,cells", [(2, 4), (3, 2)])
-def test_exact_reproduction(dim, cells):
-    s3 = O.System(dim, 3, cells, 0, 1 if dim == 2 else 0, 2).assemble()
+@pytest.mark.parametrize("dim,cells,jitter", [(2, 4, 0), (3, 2, 0), (2, 6, 1), (3, 3, 1)])
+def test_exact_reproduction(dim, cells, jitter):
+    s3 = O.System(dim, 3, cells, jitter, 1 if dim == 2 else 0, 2).assemble()
     for g in CUBIC:
         x, want = _solve_with_g(s3, g)
         assert np.abs(x - want).max() <= 1e-11 * np.abs(want).max()
-    s4 = O.System(dim, 4, cells, 0, 1 if dim == 2 else 0, 2).assemble()
+    s4 = O.System(dim, 4, cells, jitter, 1 if dim == 2 else 0, 2).assemble()
     x, want = _solve_with_g(s4, QUARTIC)
     assert np.abs(x - want).max() <= 1e-11 * np.abs(want).max()
     x, want = _solve_with_g(s3, QUARTIC)  # a quartic is not in the P3 space
@@ -130,8 +136,36 @@ def test_pattern_is_pairs_sharing_an_element(dim, degree, cells):
     assert np.all(np.diff(ci[rp[0]:rp[1]]) > 0)
 
 
-def test_p34_on_jittered_meshes_rejected():
-    with pytest.raises(ValueError):
-        O.System(2, 3, 4, jitter=1)
+def test_degree_above_4_rejected():
     with pytest.raises(ValueError):
         O.System(3, 5, 2)
+
+
+@pytest.mark.parametrize("dim,degree,cells", [(2, 3, 5), (2, 4, 3), (3, 3, 3), (3, 4, 2)])
+def test_jittered_node_coordinates_definition(dim, degree, cells):
+    s = O.System(dim, degree, cells, 1, 1 if dim == 2 else 0, 8)
+    X = s.dof_coords()
+    V = s.vertex_coords()
+    E = s.elements()
+    S = degree * cells + 1
+    Vn = cells + 1
+    for e in range(s.n_elements):
+        ids = E[e]
+        lat = np.stack([(ids // S ** d) % S for d in range(dim)], 1)
+        vmask = np.all(lat % degree == 0, axis=1)
+        vlat = lat[vmask] // degree                       # the element's vertices (cell units)
+        vid = sum(vlat[:, d] * Vn ** d for d in range(dim))
+        # barycentric weights of each node: solve N = sum_a beta_a v_a (integers)
+        M = np.vstack([vlat.T.astype(float), np.ones(dim + 1)])
+        for l in range(len(ids)):
+            beta = np.rint(np.linalg.solve(M, np.append(lat[l].astype(float), degree))).astype(int)
+            face = sorted((int(vid[a]), int(beta[a])) for a in range(dim + 1) if beta[a] > 0)
+            for d in range(dim):
+                if len(face) == 1:
+                    want = V[face[0][0], d]
+                else:
+                    t = 0.0
+                    for v, b in face:
+                        t = t + float(b) * float(V[v, d])
+                    want = t / degree
+                assert X[ids[l], d] == want

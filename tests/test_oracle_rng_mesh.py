@@ -131,5 +131,3 @@ def test_bad_specs_rejected():
         O.System(4, 1, 4)
     with pytest.raises(ValueError):
         O.System(2, 5, 4)  # degrees 1..4
-    with pytest.raises(ValueError):
-        O.System(2, 3, 4, jitter=1)  # P3/P4 on unjittered meshes only
