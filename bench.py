@@ -695,10 +695,10 @@ def run_sweep_precond():
 
 
 def run_sweep_degree():
-    """Table 7's degree study on our meshes: P1-P4 on one unjittered mesh per
-    dimension (2D 128^2 cells with random diagonals, g = sin(pi x) sinh(pi y) /
-    sinh(pi); 3D Kuhn 16^3 with the quartic harmonic Re (x+iy)^4, reproduced
-    exactly by P4 only), solved to 1e-12 (the paper's epsilon for Table 7):
+    """Table 7's degree study on our meshes: P1-P4 on a regular and a jittered
+    mesh per dimension (2D 128^2 cells with random diagonals, g = sin(pi x)
+    sinh(pi y) / sinh(pi); 3D Kuhn 16^3 with the quartic harmonic Re (x+iy)^4,
+    reproduced exactly by P4 only), solved to 1e-12 (the paper's epsilon for Table 7):
     size, nnz per row, CG iterations and time (Jacobi, block-Jacobi bs 4),
     BiCGSTAB with block-Jacobi (the paper's solver), and the nodal error
     against the exact harmonic solution."""
@@ -707,9 +707,10 @@ def run_sweep_degree():
     import paper_2201_05413_gb300 as P
     P.load()
     tol = 1e-12
-    for dim, cells, dm, gid, coef in ((2, 128, 1, 0, None), (3, 16, 0, 4, "re4")):
+    for dim, cells, dm, jit, gid, coef in ((2, 128, 1, 0, 0, None), (2, 128, 1, 1, 0, None), (3, 16, 0, 0, 4, "re4"),
+                                           (3, 16, 0, 1, 4, "re4")):
         for deg in (1, 2, 3, 4):
-            spec = (dim, deg, cells, 0, dm, 1)
+            spec = (dim, deg, cells, jit, dm, 1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             d = P.FemSystem(*spec)
@@ -722,7 +723,7 @@ def run_sweep_degree():
                 c[0, 8] = 1.0
             b = d.lift(d.dirichlet(gid, c))[:, 0]
             exact = d.dirichlet(gid, c, which="free")[:, 0]
-            row = {"sweep": "degree", "dim": dim, "cells": cells, "degree": deg, "n": A.n, "nnz": A.nnz,
+            row = {"sweep": "degree", "dim": dim, "cells": cells, "jitter": jit, "degree": deg, "n": A.n, "nnz": A.nnz,
                    "nnz_per_row": round(A.nnz / A.n, 2), "setup_ms": round(1e3 * t_setup, 1)}
             A.block_jacobi(4)
             for name, kw in (("cg", {}), ("cg_bj4", {"precond": P.GB_PC_BLOCK_JACOBI}),

@@ -75,13 +75,14 @@ typedef struct gb_allocator {
  * mix64(key + (i+1)*0x9E3779B97F4A7C15), key = seed*2^40 xor s*2^32,
  * u = (output >> 11) * 2^-53; streams 0/1/3 jitter x/y/z (i = vertex id),
  * stream 2 the diagonal (i = cell id).  degree 1..4 (P1-P4 Lagrange elements,
- * the degree study of Sec. 4.2 / Table 7; P3 and P4 on unjittered meshes
- * only): dofs are the points of the lattice with degree*cells+1 points per
- * side (the Lagrange nodes of every simplex lie on it); boundary dofs are
- * those with a coordinate 0 or degree*cells. */
+ * the degree study of Sec. 4.2 / Table 7): dofs are the points of the lattice
+ * with degree*cells+1 points per side (the Lagrange nodes of every simplex lie
+ * on it); boundary dofs are those with a coordinate 0 or degree*cells.  A
+ * P3/P4 node's coordinates are (sum of beta_a P_a over its smallest face, in
+ * ascending vertex id) / degree, correctly rounded, a vertex node the vertex. */
 typedef struct gb_fem_spec {
     int32_t dim;        /* 2 or 3 */
-    int32_t degree;     /* 1, 2, 3 or 4 (3, 4: jitter must be 0) */
+    int32_t degree;     /* 1, 2, 3 or 4 */
     int32_t cells;      /* cells per side, >= 2 */
     int32_t jitter;     /* 0 or 1 */
     int32_t diag_mode;  /* 0 fixed SW-NE, 1 random per cell (2D only) */

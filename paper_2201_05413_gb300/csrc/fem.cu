@@ -1,6 +1,5 @@
 // fem.cu -- device mesh, dof numbering, stiffness assembly, Dirichlet data
-// and lift (paper Sec. 2.2; P2-P4 as in the degree study of Sec. 4.2, P3/P4
-// on unjittered meshes).
+// and lift (paper Sec. 2.2; P2-P4 as in the degree study of Sec. 4.2).
 //
 // The mesh is implicit: a vertex's coordinates and a cell's diagonal are pure
 // functions of the lattice index and the counter-based generator, so nothing
@@ -383,9 +382,75 @@ __global__ void __launch_bounds__(128) k_fill_rows(MeshDev m, int64_t n_free, co
 // Coordinates of dof-lattice point N: a vertex, or the midpoint of the edge
 // whose endpoints round the odd coordinates down/up (in 2D, a cell-centre
 // point lies on the cell's diagonal, whose direction depends on the flip).
+// Degree >= 3: the node's smallest mesh face and its weights beta (|beta| =
+// deg) come from the simplex holding the lattice point (2D: which side of the
+// cell's diagonal; 3D: the Kuhn path of the sorted offsets -- ties put the
+// point on a shared face, whose weights are the same from either side); the
+// coordinate is (sum of beta_a P_a over that face, ascending vertex id) / deg
+// with correctly rounded operations, a vertex node the vertex itself.
+__device__ void node_coords(const MeshDev &m, const int *N, double *x) {
+    const int dm = m.deg;
+    int c[3] = {0, 0, 0}, f[3] = {0, 0, 0};
+    for (int d = 0; d < m.dim; ++d) {
+        c[d] = min(N[d] / dm, m.cells - 1);
+        f[d] = N[d] - dm * c[d];
+    }
+    int vv[4][3], bb[4];
+    int nv = m.dim + 1;
+    for (int a = 0; a < 4; ++a) for (int d = 0; d < 3; ++d) vv[a][d] = c[d];
+    if (m.dim == 2) {
+        const bool fl = cell_flipped(m, c[0] + (int64_t)m.cells * c[1]);
+        if (!fl) {  // diagonal (0,0)-(1,1)
+            if (f[0] >= f[1]) {  // (0,0), (1,0), (1,1)
+                vv[1][0] += 1; vv[2][0] += 1; vv[2][1] += 1;
+                bb[0] = dm - f[0]; bb[1] = f[0] - f[1]; bb[2] = f[1];
+            } else {             // (0,0), (1,1), (0,1)
+                vv[1][0] += 1; vv[1][1] += 1; vv[2][1] += 1;
+                bb[0] = dm - f[1]; bb[1] = f[0]; bb[2] = f[1] - f[0];
+            }
+        } else {    // diagonal (1,0)-(0,1)
+            if (f[0] + f[1] <= dm) {  // (0,0), (1,0), (0,1)
+                vv[1][0] += 1; vv[2][1] += 1;
+                bb[0] = dm - f[0] - f[1]; bb[1] = f[0]; bb[2] = f[1];
+            } else {                  // (1,0), (1,1), (0,1)
+                vv[0][0] += 1; vv[1][0] += 1; vv[1][1] += 1; vv[2][1] += 1;
+                bb[0] = dm - f[1]; bb[1] = f[0] + f[1] - dm; bb[2] = dm - f[0];
+            }
+        }
+    } else {  // Kuhn: walk the axes in decreasing offset
+        int p[3] = {0, 1, 2};
+        for (int i = 1; i < 3; ++i)
+            for (int j = i; j > 0 && f[p[j - 1]] < f[p[j]]; --j) { int t = p[j]; p[j] = p[j - 1]; p[j - 1] = t; }
+        for (int s2 = 0; s2 < 3; ++s2) {
+            for (int d = 0; d < 3; ++d) vv[s2 + 1][d] = vv[s2][d];
+            vv[s2 + 1][p[s2]] += 1;
+        }
+        bb[0] = dm - f[p[0]]; bb[1] = f[p[0]] - f[p[1]]; bb[2] = f[p[1]] - f[p[2]]; bb[3] = f[p[2]];
+    }
+    // the face: vertices with beta > 0, ascending vertex id
+    int64_t fid[4];
+    int fi[4], nf = 0;
+    for (int a = 0; a < nv; ++a) {
+        if (bb[a] <= 0) continue;
+        fid[nf] = vv[a][0] + (int64_t)m.V * (vv[a][1] + (m.dim == 3 ? (int64_t)m.V * vv[a][2] : 0));
+        fi[nf++] = a;
+    }
+    for (int i = 1; i < nf; ++i)
+        for (int j = i; j > 0 && fid[j - 1] > fid[j]; --j) {
+            int64_t t = fid[j]; fid[j] = fid[j - 1]; fid[j - 1] = t;
+            int u = fi[j]; fi[j] = fi[j - 1]; fi[j - 1] = u;
+        }
+    for (int d = 0; d < m.dim; ++d) {
+        if (nf == 1) { x[d] = vertex_coord(m, vv[fi[0]], d); continue; }
+        double t = 0.0;
+        for (int i = 0; i < nf; ++i) t = __dadd_rn(t, __dmul_rn((double)bb[fi[i]], vertex_coord(m, vv[fi[i]], d)));
+        x[d] = __ddiv_rn(t, (double)dm);
+    }
+}
+
 __device__ void dof_coords(const MeshDev &m, const int *N, double *x) {
-    if (m.deg >= 3) {  // unjittered meshes only: the refined lattice point N / (deg cells)
-        for (int d = 0; d < m.dim; ++d) x[d] = __ddiv_rn((double)N[d], (double)(m.S - 1));
+    if (m.deg >= 3) {
+        node_coords(m, N, x);
         return;
     }
     if (m.deg == 1) {
@@ -635,7 +700,6 @@ extern "C" int fem_assemble(const gb_fem_spec *spec, const gb_allocator *alloc, 
     *out = nullptr;
     GB_REQUIRE(spec->dim == 2 || spec->dim == 3, "fem_assemble: dim must be 2 or 3");
     GB_REQUIRE(spec->degree >= 1 && spec->degree <= 4, "fem_assemble: degree must be 1, 2, 3 or 4");
-    GB_REQUIRE(spec->degree <= 2 || spec->jitter == 0, "fem_assemble: P3/P4 on unjittered meshes only");
     GB_REQUIRE(spec->cells >= 2, "fem_assemble: cells must be >= 2");
     GB_REQUIRE(spec->jitter == 0 || spec->jitter == 1, "fem_assemble: jitter must be 0 or 1");
     GB_REQUIRE(spec->diag_mode == 0 || spec->diag_mode == 1, "fem_assemble: diag_mode must be 0 or 1");
