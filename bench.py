@@ -97,7 +97,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples (the JSON line carries their summary): GBPCG_CLOCKS_DIR, else a temporary directory
+        import tempfile
+        d = os.environ.get("GBPCG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"gbpcg_clocks_rank{gpu_index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
