@@ -813,7 +813,8 @@ int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const do
 
 /* ------------------------------------------------------- Block-Jacobi -- */
 /* The block-Jacobi preconditioner named among the paper's preconditioners
- * (Sec. 3.1, with BiCGSTAB; Sec. 4.1, Fig. 5): M = blockdiag(A_11, ..., A_mm),
+ * (Sec. 3.1, with BiCGSTAB; Sec. 4.1 and its accuracy-vs-epsilon figure):
+ * M = blockdiag(A_11, ..., A_mm),
  * A_jj the diagonal block of the rows [j bs, min(n, (j+1) bs)) -- bs
  * consecutive unknowns, the last block possibly shorter.  W holds each
  * block's inverse, dense row-major, nblk x bs x bs; a short last block fills

@@ -1,9 +1,10 @@
 // bjacobi.cuh -- block-Jacobi preconditioner applied inside the PCG vector
 // kernels.
 //
-// The paper's Block-Jacobi (Sec. 3.1, Sec. 4.1, Fig. 5): M = blockdiag(K_11,
-// ..., K_mm) over blocks of BS consecutive unknowns in the free-dof order,
-// applied as z = M^-1 r with the blocks' inverses.  The PCG vectors live in
+// The paper's Block-Jacobi (Sec. 3.1; Sec. 4.1 and its accuracy-vs-epsilon
+// figure): M = blockdiag(K_11, ..., K_mm) over blocks of BS consecutive
+// unknowns in the free-dof order, applied as z = M^-1 r with the blocks'
+// inverses.  The PCG vectors live in
 // SELL order, a permutation inside windows of sigma rows; with BS and sigma
 // dividing 256 every block's rows lie in one 256-row window, in both orders.
 // So one CTA takes a whole window: it updates the window's x and r, keeps r in
