@@ -307,7 +307,7 @@ def run_ours(args, rank, world):
                          "speedup_vs_f64": round(mixed_value / value * world, 3)},
         "block_jacobi_f64": {"value": round(bj_value, 4), "unit": "solves/s", "dtype": "f64",
                              "bs": BJ_BS, "speedup_vs_f64": round(bj_value / value * world, 3),
-                             "note": "block-Jacobi PCG (Sec. 3.1/4.1), block setup inside the timed step"},
+                             "note": "block-Jacobi PCG (Sec. 3.2/4.2), block setup inside the timed step"},
         "per_system": per_sys,
         "kernel_ms": {"f64": {"spmv_pq": ms64[0], "update": ms64[1], "pupdate": ms64[2]},
                       "f32": {"spmv_pq": ms32[0], "update": ms32[1], "pupdate": ms32[2]}},

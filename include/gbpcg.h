@@ -199,8 +199,8 @@ int sell_autotune(const gb_fem_system *sys, const double *d_b, int precision, in
  * another value. */
 int sell_set_variant(gb_sell *A, int variant);
 
-/* Block-Jacobi preconditioner (the paper's Block-Jacobi, Sec. 3.1 and Sec.
- * 4.1): M = blockdiag(K_11, ..., K_mm), K_jj the diagonal block of the bs
+/* Block-Jacobi preconditioner (the paper's Block-Jacobi, Sec. 3.2 and Sec.
+ * 4.2): M = blockdiag(K_11, ..., K_mm), K_jj the diagonal block of the bs
  * consecutive free dofs [j bs, min(n, (j+1) bs)) in the original (free-dof)
  * order; the last block is shorter when bs does not divide n.
  * sell_block_jacobi computes each block's inverse on the device (Gauss-Jordan
@@ -256,7 +256,7 @@ int sell_block_jacobi_apply(const gb_sell *A, const double *d_x, double *d_y, vo
 enum { GB_F64 = 0, GB_F32_IR = 1, GB_BF16_IR = 2, GB_F32_RU = 3, GB_BF16_RU = 4 };
 enum { GB_PC_JACOBI = 0, GB_PC_BLOCK_JACOBI = 1 };
 /* method GB_BICGSTAB: BiCGSTAB (van der Vorst), the Krylov method of the
- * paper's experiments (Sec. 3.1), preconditioned on the right with the
+ * paper's experiments (Sec. 3.2), preconditioned on the right with the
  * Jacobi or block-Jacobi M: two SpMVs and two preconditioner applications per
  * step (stats.iterations counts steps); the stop is confirmed on the true
  * residual as for CG.  pcg_solve with GB_F64 on C = 32 layouts (GB_EINVAL

@@ -813,7 +813,7 @@ int orc_cholesky_solve(int64_t n, const int64_t *rp, const int32_t *ci, const do
 
 /* ------------------------------------------------------- Block-Jacobi -- */
 /* The block-Jacobi preconditioner named among the paper's preconditioners
- * (Sec. 3.1, with BiCGSTAB; Sec. 4.1 and its accuracy-vs-epsilon figure):
+ * (Sec. 3.2, with BiCGSTAB; Sec. 4.2 and its accuracy-vs-epsilon figure):
  * M = blockdiag(A_11, ..., A_mm),
  * A_jj the diagonal block of the rows [j bs, min(n, (j+1) bs)) -- bs
  * consecutive unknowns, the last block possibly shorter.  W holds each
@@ -886,7 +886,7 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
 }
 
 /* ------------------------------------------------------------ BiCGSTAB -- */
-/* BiCGSTAB (van der Vorst 1992), the Krylov method the paper runs (Sec. 3.1),
+/* BiCGSTAB (van der Vorst 1992), the Krylov method the paper runs (Sec. 3.2),
  * with the preconditioner applied on the right (x = M^{-1} y):
  *   r = b - A x, rh = r (shadow residual), rho0 = alpha = omega = 1, p = v = 0
  *   repeat: rho = rh.r; beta = (rho/rho0)(alpha/omega);

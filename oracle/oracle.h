@@ -81,7 +81,7 @@ int orc_pcg(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
             const double *b, double *x, double tol, int64_t maxit,
             int64_t *iters, double *relres);
 
-/* Block-Jacobi (Sec. 3.1, Sec. 4.1): M = blockdiag of the diagonal blocks of
+/* Block-Jacobi (Sec. 3.2, Sec. 4.2): M = blockdiag of the diagonal blocks of
  * bs consecutive rows (the last one shorter when bs does not divide n).
  * orc_bjacobi writes each block's inverse, dense row-major, into W
  * (ceil(n/bs) x bs x bs; a short block fills its leading corner, the rest 0);
@@ -94,7 +94,7 @@ int orc_pcg_bj(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                const double *b, double *x, double tol, int64_t maxit, int64_t *iters,
                double *relres);
 
-/* BiCGSTAB (Sec. 3.1's Krylov method), right-preconditioned: bs <= 1 Jacobi,
+/* BiCGSTAB (Sec. 3.2's Krylov method), right-preconditioned: bs <= 1 Jacobi,
  * bs >= 2 block-Jacobi over blocks of bs rows (orc_bjacobi).  Any nonsingular
  * CSR matrix.  Stops on Eq. (2), confirmed on the true residual (restart from
  * it otherwise).  Returns 0 converged, 1 not converged in maxit steps, 2

@@ -1,5 +1,5 @@
 // bicgstab.cuh -- BiCGSTAB kernels (van der Vorst 1992), the Krylov method
-// the paper runs (Sec. 3.1), right-preconditioned with Jacobi or block-Jacobi:
+// the paper runs (Sec. 3.2), right-preconditioned with Jacobi or block-Jacobi:
 //   rho = r^.r;  beta = (rho/rho0)(alpha/omega);  p = r + beta (p - omega v);
 //   ph = M^-1 p;  v = A ph;  alpha = rho / r^.v;  s = r - alpha v;
 //   (||s|| <= tol ||b||: x += alpha ph, stop);  sh = M^-1 s;  t = A sh;

@@ -1,5 +1,5 @@
 // bjacobi.cu -- setup of the block-Jacobi preconditioner of a SELL matrix
-// (the paper's Block-Jacobi, Sec. 3.1 and Sec. 4.1) and its C entry points.
+// (the paper's Block-Jacobi, Sec. 3.2 and Sec. 4.2) and its C entry points.
 // The apply runs inside the PCG kernels (bjacobi.cuh).
 #include <cstring>
 

@@ -1,7 +1,7 @@
 // bjacobi.cuh -- block-Jacobi preconditioner applied inside the PCG vector
 // kernels.
 //
-// The paper's Block-Jacobi (Sec. 3.1; Sec. 4.1 and its accuracy-vs-epsilon
+// The paper's Block-Jacobi (Sec. 3.2; Sec. 4.2 and its accuracy-vs-epsilon
 // figure): M = blockdiag(K_11, ..., K_mm) over blocks of BS consecutive
 // unknowns in the free-dof order, applied as z = M^-1 r with the blocks'
 // inverses.  The PCG vectors live in

@@ -1,4 +1,4 @@
-"""GPU parity: BiCGSTAB (the paper's Krylov method, Sec. 3.1), right-
+"""GPU parity: BiCGSTAB (the paper's Krylov method, Sec. 3.2), right-
 preconditioned with Jacobi or block-Jacobi, against the oracle's BiCGSTAB and
 the exact solutions.
 

@@ -1,5 +1,5 @@
 """GPU parity: the block-Jacobi preconditioner (the paper's Block-Jacobi,
-Sec. 3.1 and Sec. 4.1) against the oracle.
+Sec. 3.2 and Sec. 4.2) against the oracle.
 
 - the device's block inverses (Gauss-Jordan, symmetrised, packed) equal the
   oracle's (Cholesky solves against unit vectors) to 1e-12 of each block's

@@ -1,4 +1,4 @@
-"""Pins of the oracle's BiCGSTAB (the paper's Krylov method, Sec. 3.1; right
+"""Pins of the oracle's BiCGSTAB (the paper's Krylov method, Sec. 3.2; right
 preconditioning with Jacobi or block-Jacobi) against facts that do not depend
 on the oracle:
 

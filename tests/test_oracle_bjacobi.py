@@ -1,5 +1,5 @@
 """Pins of the oracle's block-Jacobi preconditioner (the paper's Block-Jacobi,
-Sec. 3.1 and Sec. 4.1) against facts that do not depend on the oracle:
+Sec. 3.2 and Sec. 4.2) against facts that do not depend on the oracle:
 
 - each stored block times the matrix's diagonal block is the identity, and the
   blocks are symmetric;
