@@ -6,7 +6,10 @@ Bar: Eq. (2) at 1e-10 (recomputed here in fp64 from the oracle's matrix),
 Eq. (1) error <= 1e-8 against the oracle's solution at 1e-13, and the oracle's
 step count up to rounding drift (BiCGSTAB's residual is not monotone and its
 true-residual restarts depend on rounding, so the drift is allowed 15 %); one step with the exact preconditioner; tiny systems
-within n steps; graph and direct launches give the same bits."""
+within n steps; graph and direct launches give the same bits; the restart
+after a breakdown (and the breakdown report when the residual has not fallen)
+on matrices where the zero is exact, with the oracle's step and restart
+counts; non-symmetric matrices against the oracle."""
 import numpy as np
 import pytest
 
@@ -101,3 +104,76 @@ def test_bad_arguments(P):
         A.solve(b, method=5)
     with pytest.raises(P.GbError):
         P.pcg_solve_batched([A], [b], method=P.GB_BICGSTAB)
+
+
+def _raw(P, rp, ci, v):
+    import torch
+    return P.Sell.from_csr(torch.tensor(rp, dtype=torch.int32, device="cuda"),
+                           torch.tensor(ci, dtype=torch.int32, device="cuda"),
+                           torch.tensor(v, dtype=torch.float64, device="cuda"), 32, 256)
+
+
+def test_breakdown_after_progress_restarts_like_the_oracle(P):
+    """The matrix whose second shadow product is exactly zero (after the
+    residual fell to sqrt(0.1)): the device restarts once from the true
+    residual, as the oracle does, and reaches the dense solution."""
+    import torch
+    from test_oracle_bicgstab import (BREAK_AFTER_PROGRESS, BREAK_AFTER_PROGRESS_B, BREAK_AFTER_PROGRESS_X,
+                                      dense_csr)
+    rp, ci, v = dense_csr(BREAK_AFTER_PROGRESS)
+    A = _raw(P, rp, ci, v)
+    b = torch.tensor(BREAK_AFTER_PROGRESS_B, device="cuda")
+    x, st = A.solve(b, tol=1e-13, max_iter=100, method=P.GB_BICGSTAB)
+    xo, sto, ito, _ = O.bicgstab(rp, ci, v, BREAK_AFTER_PROGRESS_B, tol=1e-13)
+    assert st["status"] == 0 and sto == 0
+    assert st["restarts"] == 1
+    assert st["iterations"] == ito
+    assert np.abs(x.cpu().numpy() - BREAK_AFTER_PROGRESS_X).max() <= 1e-14
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-14
+
+
+def test_breakdown_without_progress_is_reported_like_the_oracle(P):
+    """rho_hat.v exactly zero in the first step: GB_BREAKDOWN after 0 steps,
+    x = x0 = 0, on both sides."""
+    import torch
+    from test_oracle_bicgstab import BREAK_AT_ONCE, BREAK_AT_ONCE_B, dense_csr
+    rp, ci, v = dense_csr(BREAK_AT_ONCE)
+    A = _raw(P, rp, ci, v)
+    b = torch.tensor(BREAK_AT_ONCE_B, device="cuda")
+    x, st = A.solve(b, tol=1e-12, max_iter=100, method=P.GB_BICGSTAB, raise_on_fail=False)
+    xo, sto, ito, relo = O.bicgstab(rp, ci, v, BREAK_AT_ONCE_B, tol=1e-12)
+    assert sto == 2 and ito == 0
+    assert st["rc"] == P.gbpcg.GB_BREAKDOWN and st["status"] == P.gbpcg.GB_BREAKDOWN
+    assert st["iterations"] == 0 and st["restarts"] == 0
+    assert bool((x == 0).all()) and abs(st["relres"] - relo) <= 1e-15
+
+
+@pytest.mark.parametrize("case,c", [((2, 1, 16, 1, 1, 4), 0.3), ((2, 2, 8, 1, 1, 2), 0.5),
+                                    ((2, 2, 8, 1, 1, 2), 0.9), ((3, 1, 6, 1, 0, 3), 0.2),
+                                    ((2, 1, 64, 1, 1, 5), 0.5), ((2, 2, 40, 1, 1, 6), 0.7)])
+def test_nonsymmetric_matrix_matches_oracle(P, case, c):
+    """K + c S with S antisymmetric on K's pattern (S_ij = -S_ji = |K_ij| for
+    i < j), a convection-like non-symmetric matrix with K as its symmetric
+    part: the device BiCGSTAB (Jacobi on the right) against the oracle's
+    BiCGSTAB at 1e-13, itself checked against numpy's dense solve where n <= 2000."""
+    import torch
+    s = O.System(*case).assemble()
+    rp, ci, v = s.k_ii()
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    v2 = v + c * np.sign(ci - rows) * np.abs(v)
+    b = np.random.default_rng(5).standard_normal(n)
+    A = _raw(P, rp, ci, v2)
+    x, st = A.solve(torch.tensor(b, device="cuda"), tol=TOL, max_iter=20 * n + 100, method=P.GB_BICGSTAB)
+    xd = x.cpu().numpy()
+    assert st["status"] == 0
+    assert np.linalg.norm(b - O.spmv(rp, ci, v2, xd)) / np.linalg.norm(b) <= 1.5 * TOL
+    xo, sto, ito, _ = O.bicgstab(rp, ci, v2, b, tol=1e-13)
+    assert sto == 0
+    if n <= 2000:
+        M = np.zeros((n, n))
+        M[rows, ci] = v2
+        assert O.x_err(np.linalg.solve(M, b), xo) <= 1e-11
+    assert O.x_err(xo, xd) <= XERR
+    xo10, sto10, ito10, _ = O.bicgstab(rp, ci, v2, b, tol=TOL)
+    assert abs(st["iterations"] - ito10) <= max(5, 0.15 * ito10), (st["iterations"], ito10)

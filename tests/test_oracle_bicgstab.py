@@ -10,7 +10,13 @@ on the oracle:
 - it does not rely on symmetry: on a non-symmetric matrix (the SPD matrix plus
   an antisymmetric part on its pattern, a convection-like term) it reaches
   numpy's dense solution;
-- b = 0 gives x = 0 without iterating.
+- b = 0 gives x = 0 without iterating;
+- a breakdown (a zero shadow product) after the residual has fallen restarts
+  the recurrence from the true residual with a new shadow vector and reaches
+  the dense solution; a breakdown before the residual has fallen below 0.9 of
+  the starting one is reported (status 2) instead of restarting forever.  Both
+  cases are 3x3 / 2x2 matrices built so that the zero happens exactly, in
+  every rounding order, at a known step.
 """
 import numpy as np
 import pytest
@@ -82,3 +88,54 @@ def test_zero_rhs():
     s, rp, ci, v = _K((2, 1, 10, 1, 1, 1))
     x, st, it, rel = O.bicgstab(rp, ci, v, np.zeros(len(rp) - 1), x0=np.ones(len(rp) - 1))
     assert st == 0 and it == 0 and np.all(x == 0)
+
+
+def dense_csr(A):
+    """CSR of a small dense matrix (its diagonal always stored)."""
+    n = A.shape[0]
+    rp, ci, v = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if A[i, j] != 0.0 or i == j:
+                ci.append(j)
+                v.append(A[i, j])
+        rp.append(len(ci))
+    return np.array(rp, np.int64), np.array(ci, np.int32), np.array(v)
+
+
+# Breakdown after progress.  Row 0 of A is e0^T and b = e0, so the first step
+# has alpha = (b.b)/(b.Ab) = 1 and s = b - Ab with s_0 = 0; then t_0 = (As)_0
+# = s_0 = 0 and the new residual r = s - omega t has r_0 = 0, so the next
+# shadow product rho = b.r = r_0 is exactly zero (rounding cannot change a
+# sum of exact zeros).  omega = 0.8 and ||r|| = sqrt(0.1) < 0.9 ||b||: the
+# residual has fallen, the recurrence restarts from x = (1, -0.4, -0.4) and,
+# with r_0 = 0, runs on the 2x2 block [[1, 0.5], [-0.5, 1]] (BiCG there ends
+# within two steps).  Solution: (1, -0.2, -0.6).
+BREAK_AFTER_PROGRESS = np.array([[1.0, 0.0, 0.0], [0.5, 1.0, 0.5], [0.5, -0.5, 1.0]])
+BREAK_AFTER_PROGRESS_B = np.array([1.0, 0.0, 0.0])
+BREAK_AFTER_PROGRESS_X = np.array([1.0, -0.2, -0.6])
+
+# Breakdown before progress.  A = [[1, 2], [0, -1]], Jacobi M^-1 = diag(1, -1),
+# b = (1, 1): p = b, ph = (1, -1), v = A ph = (-1, 1) and rho_hat.v = b.v = 0
+# exactly in the first step.  The true residual is still ||b||: nothing to
+# restart from, so the solve reports a breakdown after 0 steps.
+BREAK_AT_ONCE = np.array([[1.0, 2.0], [0.0, -1.0]])
+BREAK_AT_ONCE_B = np.array([1.0, 1.0])
+
+
+def test_breakdown_after_progress_restarts_to_the_solution():
+    rp, ci, v = dense_csr(BREAK_AFTER_PROGRESS)
+    assert np.allclose(np.linalg.solve(BREAK_AFTER_PROGRESS, BREAK_AFTER_PROGRESS_B), BREAK_AFTER_PROGRESS_X,
+                       rtol=0, atol=1e-15)
+    x, st, it, rel = O.bicgstab(rp, ci, v, BREAK_AFTER_PROGRESS_B, tol=1e-13)
+    assert st == 0 and rel <= 1e-13
+    # one step before the breakdown, at most two on the 2x2 block after it
+    assert 2 <= it <= 3
+    assert np.abs(x - BREAK_AFTER_PROGRESS_X).max() <= 1e-14
+
+
+def test_breakdown_without_progress_is_reported():
+    rp, ci, v = dense_csr(BREAK_AT_ONCE)
+    x, st, it, rel = O.bicgstab(rp, ci, v, BREAK_AT_ONCE_B, tol=1e-12)
+    assert st == 2 and it == 0
+    assert np.all(x == 0.0) and rel == 1.0

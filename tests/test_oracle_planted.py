@@ -1,4 +1,5 @@
-"""The pins of the block-Jacobi, block CG, BiCGSTAB and P3/P4 oracle functions
+"""The pins of the block-Jacobi, block CG, BiCGSTAB (its steps and its restart
+after a breakdown) and P3/P4 oracle functions
 catch plausible mistakes: each test builds a wrong variant (in numpy, on the
 CPU) and shows that the pin that passes for the oracle rejects it."""
 import math
@@ -7,6 +8,8 @@ import numpy as np
 
 import oracle as O
 
+from test_oracle_bicgstab import (BREAK_AFTER_PROGRESS, BREAK_AFTER_PROGRESS_B, BREAK_AFTER_PROGRESS_X,
+                                   BREAK_AT_ONCE, BREAK_AT_ONCE_B)
 from test_oracle_bjacobi import _tridiag_inverse, _dense_block
 from test_oracle_p34 import _stiffness_by_quadrature, _elem_vertices
 
@@ -156,3 +159,86 @@ def test_p3_quadrature_pin_rejects_transposed_nodes():
     wrong[[1, 2]] = wrong[[2, 1]]  # two edge nodes swapped
     Kw = _stiffness_by_quadrature(wrong, P, 3)
     assert np.abs(Ko - Kw).max() > 1e-3 * np.abs(Kq).max()
+
+
+def _bicgstab_restarting(A, b, tol, maxit=100, restart="oracle"):
+    """Jacobi BiCGSTAB with the oracle's breakdown rule (restart from the true
+    residual with a new shadow vector while the residual has fallen below 0.9
+    of the one the recurrence started from; else report status 2), and three
+    planted mistakes: restart="none" (a breakdown ends the solve), "keep_shadow"
+    (the restart keeps the old shadow vector), "no_guard" (restart however
+    little the residual fell).  Returns (x, status, steps)."""
+    d = 1.0 / np.diag(A)
+    x = np.zeros_like(b)
+    bn = np.linalg.norm(b)
+    it, restarts, broke, rel_start = 0, 0, False, np.inf
+    rh = None
+    while True:
+        r = b - A @ x
+        rel = np.linalg.norm(r) / bn
+        if rel <= tol:
+            return x, 0, it
+        if it >= maxit or restarts > 50:
+            return x, 1, it
+        if broke and (restart == "none" or (restart != "no_guard" and not rel < 0.9 * rel_start)):
+            return x, 2, it
+        broke, rel_start = False, rel
+        if rh is not None:  # every start after the first is a restart
+            restarts += 1
+        if rh is None or restart != "keep_shadow":
+            rh = r.copy()
+        p = np.zeros_like(b)
+        vv = np.zeros_like(b)
+        rho0 = alpha = omega = 1.0
+        while it < maxit:
+            rho = rh @ r
+            if rho == 0.0:
+                broke = True
+                break
+            p = r + (rho / rho0) * (alpha / omega) * (p - omega * vv)
+            ph = d * p
+            vv = A @ ph
+            rv = rh @ vv
+            if rv == 0.0:
+                broke = True
+                break
+            alpha = rho / rv
+            s = r - alpha * vv
+            it += 1
+            if np.linalg.norm(s) <= tol * bn:
+                x = x + alpha * ph
+                break
+            sh = d * s
+            t = A @ sh
+            omega = (t @ s) / (t @ t)
+            x = x + alpha * ph + omega * sh
+            r = s - omega * t
+            if np.linalg.norm(r) <= tol * bn:
+                break
+            rho0 = rho
+        else:
+            return x, 1, it
+
+
+def test_bicgstab_restart_pin_rejects_no_restart_and_stale_shadow():
+    """After a breakdown that follows progress the oracle restarts and reaches
+    the solution; ending the solve at the breakdown, or restarting with the
+    old shadow vector (whose product with the new residual is zero again),
+    report a breakdown instead."""
+    A, b, xs = BREAK_AFTER_PROGRESS, BREAK_AFTER_PROGRESS_B, BREAK_AFTER_PROGRESS_X
+    x, st, it = _bicgstab_restarting(A, b, 1e-13)
+    assert st == 0 and np.abs(x - xs).max() <= 1e-14
+    for wrong in ("none", "keep_shadow"):
+        x, st, it = _bicgstab_restarting(A, b, 1e-13, restart=wrong)
+        assert st == 2 and np.abs(x - xs).max() > 0.1, wrong
+
+
+def test_bicgstab_breakdown_pin_rejects_unguarded_restart():
+    """A breakdown before any progress is reported after 0 steps by the oracle;
+    restarting without the 0.9 test repeats the same breakdown until the
+    restart cap and returns 'not converged' (status 1) instead."""
+    A, b = BREAK_AT_ONCE, BREAK_AT_ONCE_B
+    x, st, it = _bicgstab_restarting(A, b, 1e-12)
+    assert st == 2 and it == 0
+    x, st, it = _bicgstab_restarting(A, b, 1e-12, restart="no_guard")
+    assert st == 1
