@@ -381,7 +381,15 @@ typedef struct ServeStats {
     int32_t max_resident, reserved;
 } ServeStats;
 
-int serve_create(const ServeOptions *opt, gb_server **out);
+/* alloc: where the requests' device memory (their matrices, right-hand sides
+ * and Krylov state) comes from -- the caller's allocator, called from the
+ * server's own thread (so it must be thread-safe), or NULL for a
+ * stream-ordered pool (cudaMallocAsync).  Either way the bytes are counted
+ * against mem_budget.  The server's fixed tables (max_slots descriptors) use
+ * cudaMalloc.  The caller's current device is left as it was.  Errors:
+ * GB_EINVAL (options, an allocator without alloc/free), GB_ENOMEM, GB_ECUDA;
+ * nothing stays allocated after an error. */
+int serve_create(const ServeOptions *opt, const gb_allocator *alloc, gb_server **out);
 /* Non-blocking: queues the request and returns its ticket (> 0). */
 int serve_submit(gb_server *srv, const ServeRequest *req, uint64_t *ticket);
 /* GB_PENDING while the request runs; then its final status with *out filled

@@ -333,7 +333,9 @@ class Server:
         import numpy as np  # noqa: F401
         o = G.ServeOptions(int(mem_budget), max_slots, precision, tol, max_iter, iters_per_step, device)
         h = C.c_void_p()
-        G.check(G.lib().serve_create(C.byref(o), C.byref(h)), "serve_create")
+        # no caller allocator: the server allocates from its own stream-ordered
+        # pool (its thread would otherwise call back into Python)
+        G.check(G.lib().serve_create(C.byref(o), None, C.byref(h)), "serve_create")
         self.handle = h
         self._live = {}
 

@@ -107,7 +107,8 @@ struct gb_server {
     size_t in_use = 0, peak = 0;
     size_t slot_bytes_acc = 0;  // bytes allocated while admitting the current slot
     std::unordered_map<void *, size_t> sizes;
-    gb_allocator alloc{};
+    gb_allocator alloc{};  // what the slots' assembly and SELL build allocate through (srv_alloc)
+    gb_allocator user{};   // the caller's allocator (serve_create), or none: the stream-ordered pool
     // table buffers (main stream)
     gb::BSys *d_sys = nullptr;
     int *d_unit_sys = nullptr, *d_mask = nullptr;
@@ -128,11 +129,17 @@ struct gb_server {
 using namespace gb;
 
 // ------------------------------------------------------------- allocator --
-// Stream-ordered pool allocations on the side stream, counted per slot.
+// Allocations on the side stream, counted per slot: through the caller's
+// allocator when serve_create was given one, else from the stream-ordered pool.
 static void *srv_alloc(void *ctx, size_t bytes, void *stream) {
     gb_server *s = (gb_server *)ctx;
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) return nullptr;
+    if (s->user.alloc) {
+        p = s->user.alloc(s->user.ctx, bytes, stream);
+        if (!p) return nullptr;
+    } else if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) {
+        return nullptr;
+    }
     s->sizes[p] = bytes;
     s->in_use += bytes;
     s->slot_bytes_acc += bytes;
@@ -147,7 +154,8 @@ static void srv_free(void *ctx, void *p, void *stream) {
         s->in_use -= it->second;
         s->sizes.erase(it);
     }
-    cudaFreeAsync(p, (cudaStream_t)stream);
+    if (s->user.free) s->user.free(s->user.ctx, p, stream);
+    else cudaFreeAsync(p, (cudaStream_t)stream);
 }
 
 template <class T>
@@ -781,34 +789,60 @@ static void server_loop(gb_server *s) {
 }
 
 // ================================================================= ABI ==
-extern "C" int serve_create(const ServeOptions *opt, gb_server **out) {
+// Releases what serve_create made of a server whose thread never started.
+static void release_unstarted(gb_server *s) {
+    cudaFree(s->d_sys); cudaFree(s->d_mask); cudaFree(s->d_G); cudaFree(s->d_sys1); cudaFree(s->d_mask1);
+    if (s->ev) cudaEventDestroy(s->ev);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->main_st) cudaStreamDestroy(s->main_st);
+    if (s->side_st) cudaStreamDestroy(s->side_st);
+    delete s;
+}
+
+extern "C" int serve_create(const ServeOptions *opt, const gb_allocator *alloc, gb_server **out) {
     GB_REQUIRE(opt && out, "serve_create: NULL argument");
     *out = nullptr;
     GB_REQUIRE(opt->mem_budget >= (1u << 20), "serve_create: mem_budget below 1 MB");
     GB_REQUIRE(opt->max_slots >= 1 && opt->max_slots <= 4096, "serve_create: max_slots not in 1..4096");
     GB_REQUIRE(opt->precision == GB_F64 || opt->precision == GB_F32_RU,
                "serve_create: precision must be GB_F64 or GB_F32_RU");
+    GB_REQUIRE(!alloc || (alloc->alloc && alloc->free), "serve_create: allocator without alloc/free");
+    int prev = 0;
+    GB_CHECK_CUDA(cudaGetDevice(&prev));
     gb_server *s = new gb_server();
     s->opt = *opt;
+    if (alloc) s->user = *alloc;
     if (!(s->opt.tol > 0)) s->opt.tol = 1e-10;
     if (s->opt.max_iter <= 0) s->opt.max_iter = 1000000;
     if (s->opt.iters_per_step < 0) s->opt.iters_per_step = 0;
-    if (opt->device >= 0) GB_CHECK_CUDA(cudaSetDevice(opt->device));
-    GB_CHECK_CUDA(cudaGetDevice(&s->dev));
-    GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->main_st, cudaStreamNonBlocking));
-    GB_CHECK_CUDA(cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking));
-    GB_CHECK_CUDA(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
-    GB_CHECK_CUDA(cudaEventCreate(&s->ev0));
-    GB_CHECK_CUDA(cudaEventCreate(&s->ev1));
     s->alloc.ctx = s;
     s->alloc.alloc = srv_alloc;
     s->alloc.free = srv_free;
-    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_sys, sizeof(BSys) * s->opt.max_slots));
-    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_mask, sizeof(int) * KMAX * s->opt.max_slots));
-    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_G, sizeof(BGlobal)));
-    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_sys1, sizeof(BSys)));
-    GB_CHECK_CUDA(cudaMalloc((void **)&s->d_mask1, sizeof(int) * KMAX));
+    const char *what = nullptr;
+    cudaError_t e = cudaSuccess;
+#define GB_SC(expr) if (e == cudaSuccess && (e = (expr)) != cudaSuccess) what = #expr
+    if (opt->device >= 0) GB_SC(cudaSetDevice(opt->device));
+    GB_SC(cudaGetDevice(&s->dev));
+    GB_SC(cudaStreamCreateWithFlags(&s->main_st, cudaStreamNonBlocking));
+    GB_SC(cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking));
+    GB_SC(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
+    GB_SC(cudaEventCreate(&s->ev0));
+    GB_SC(cudaEventCreate(&s->ev1));
+    GB_SC(cudaMalloc((void **)&s->d_sys, sizeof(BSys) * s->opt.max_slots));
+    GB_SC(cudaMalloc((void **)&s->d_mask, sizeof(int) * KMAX * s->opt.max_slots));
+    GB_SC(cudaMalloc((void **)&s->d_G, sizeof(BGlobal)));
+    GB_SC(cudaMalloc((void **)&s->d_sys1, sizeof(BSys)));
+    GB_SC(cudaMalloc((void **)&s->d_mask1, sizeof(int) * KMAX));
+#undef GB_SC
+    if (e != cudaSuccess) {
+        set_error("serve_create: %s: %s", what, cudaGetErrorString(e));
+        release_unstarted(s);
+        cudaSetDevice(prev);
+        return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
+    }
     s->th = std::thread(server_loop, s);
+    cudaSetDevice(prev);
     *out = s;
     return GB_OK;
 }

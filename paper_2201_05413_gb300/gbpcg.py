@@ -149,7 +149,7 @@ _SIGS = {
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_solve_noalloc": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "pcg_kernel_times": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_double)]),
-    "serve_create": (C.c_int, [C.POINTER(ServeOptions), C.POINTER(_P)]),
+    "serve_create": (C.c_int, [C.POINTER(ServeOptions), _P, C.POINTER(_P)]),
     "serve_submit": (C.c_int, [_P, C.POINTER(ServeRequest), C.POINTER(C.c_uint64)]),
     "serve_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(ServeResult)]),
     "serve_stats": (C.c_int, [_P, C.POINTER(ServeStats)]),
