@@ -20,20 +20,46 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def _compile(out, extra, force):
+    if force or not os.path.exists(out) or os.path.getmtime(out) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off"] + extra +
+                              ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (no FMA contraction, single thread)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    """Compile oracle.c with gcc (no FMA contraction, single thread): the
+    pinned oracle.  Also compiles the same source with -fopenmp into
+    liboracle_omp.so, a timing build for the all-core CPU baseline only."""
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
 
 
 _lib = None
+_lib_omp = None
+
+
+def lib_omp(threads):
+    """The OpenMP timing build of the same source (the all-core CPU baseline;
+    nothing is checked against it), set to `threads` threads."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        L = C.CDLL(_LIB_OMP)
+        P = C.POINTER
+        L.orc_pcg.restype = C.c_int
+        L.orc_pcg.argtypes = [C.c_int64, P(C.c_int64), P(C.c_int32), P(C.c_double), P(C.c_double),
+                              P(C.c_double), C.c_double, C.c_int64, P(C.c_int64), P(C.c_double)]
+        L.omp_set_num_threads.argtypes = [C.c_int]
+        _lib_omp = L
+    _lib_omp.omp_set_num_threads(int(threads))
+    return _lib_omp
 
 
 def lib():
@@ -213,9 +239,10 @@ def spmv(rp, ci, v, x):
     return y
 
 
-def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None):
+def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None, threads=None):
     """PCG to ||b-Ax||/||b|| <= tol (Eq. 2) with the Jacobi preconditioner, or
     with block-Jacobi over blocks of bs consecutive rows when bs is given.
+    threads (Jacobi only): run the OpenMP timing build on that many threads.
     Returns (x, status, iters, relres)."""
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -225,7 +252,10 @@ def pcg(rp, ci, v, b, tol=1e-10, maxit=None, x0=None, bs=None):
     maxit = 20 * n + 100 if maxit is None else maxit
     args = (_p(b, C.c_double), _p(x, C.c_double), tol, maxit, _p(it, C.c_int64), _p(rr, C.c_double))
     A = (n, _p(rp, C.c_int64), _p(ci, C.c_int32), _p(v, C.c_double))
-    st = lib().orc_pcg(*A, *args) if bs is None else lib().orc_pcg_bj(*A, int(bs), *args)
+    if threads:
+        st = lib_omp(threads).orc_pcg(*A, *args)
+    else:
+        st = lib().orc_pcg(*A, *args) if bs is None else lib().orc_pcg_bj(*A, int(bs), *args)
     return x, int(st), int(it[0]), float(rr[0])
 
 

@@ -13,6 +13,11 @@
  * Dirichlet dofs are eliminated, leaving the SPD system K_II u = -K_IB g_B,
  * which is solved by CG with the Jacobi preconditioner M = diag(K_II)
  * (preconditioned Krylov solve, Sec. 2.1) to the relative residual of Eq. (2).
+ *
+ * The `omp` pragmas on the CG loops are inert in the pinned build above (no
+ * -fopenmp); the benchmark's all-core CPU baseline compiles this same source
+ * a second time with -fopenmp for timing only (its dot products then sum in
+ * per-thread pieces, so its rounding differs from the single-thread build's).
  */
 #include "oracle.h"
 
@@ -666,6 +671,7 @@ void orc_lift(const orc_sys *s, const double *gB, int k, double *b) {
 /* -------------------------------------------------------------- solvers -- */
 void orc_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
               const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double t = 0.0;
         for (int64_t k = rp[i]; k < rp[i + 1]; ++k) t += v[k] * x[ci[k]];
@@ -675,6 +681,7 @@ void orc_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
 
 static double dot(int64_t n, const double *a, const double *b) {
     double t = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : t)
     for (int64_t i = 0; i < n; ++i) t += a[i] * b[i];
     return t;
 }
@@ -685,6 +692,7 @@ typedef void (*precond_fn)(int64_t n, const void *ctx, const double *r, double *
 /* Jacobi: M = diag(A), ctx = 1/A_ii */
 static void jacobi_apply(int64_t n, const void *ctx, const double *r, double *z) {
     const double *dinv = (const double *)ctx;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
 }
 
@@ -713,11 +721,13 @@ static int pcg_core(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
     int64_t it = 0;
     int restarts = 0;
     orc_spmv(n, rp, ci, v, x, q);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
     double rel = sqrt(dot(n, r, r)) / bn;
     while (status == 1) {
         if (rel <= tol) { status = 0; break; }
         apply(n, ctx, r, z);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) p[i] = z[i];
         double rho = dot(n, r, z);
         int restart = 0;
@@ -726,11 +736,13 @@ static int pcg_core(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
             const double pq = dot(n, p, q);
             if (!(pq > 0.0) || !isfinite(pq)) { status = 2; break; }
             const double alpha = rho / pq;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
             ++it;
             rel = sqrt(dot(n, r, r)) / bn;
             if (rel <= tol) {
                 orc_spmv(n, rp, ci, v, x, q);
+#pragma omp parallel for schedule(static)
                 for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
                 const double tr = sqrt(dot(n, q, q)) / bn;
                 if (tr <= tol) { rel = tr; status = 0; break; }
@@ -743,6 +755,7 @@ static int pcg_core(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
             const double rho1 = dot(n, r, z);
             const double beta = rho1 / rho;
             rho = rho1;
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         }
         if (status != 1) break;
