@@ -52,6 +52,10 @@ const char *gbpcg_version(void);
 /* Kernels this process has launched through the library so far (launches
  * replayed by a CUDA graph's loop included). */
 int64_t gbpcg_kernel_launches(void);
+/* Device allocations the library's solvers, assembly and format conversion
+ * have made so far in this process (through a caller's gb_allocator or
+ * cudaMalloc); a call that allocates nothing leaves it unchanged. */
+int64_t gbpcg_device_allocations(void);
 
 /* Device memory supplier.  alloc(ctx, bytes, stream) returns a device pointer
  * aligned to at least 256 bytes, or NULL; free(ctx, ptr, stream) releases it.
@@ -277,7 +281,9 @@ typedef struct PcgOptions {
     int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
     int32_t persist_off;   /* pcg_solve_batched: 0 (default) = systems with n * k2 <= 32768 (k2: the
                               power of two >= k) are solved whole by one CTA each in a single
-                              persistent launch; 1 = every system in the multi-launch loop */
+                              persistent launch, and systems with n * k2 <= 524288 by one
+                              thread-block cluster of 8 CTAs each in another; 1 = every system in
+                              the multi-launch loop; 2 = the CTA-local tier only */
     int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
     int32_t method;        /* GB_CG (0, default) or GB_BICGSTAB (pcg_solve, GB_F64, C = 32) */
 } PcgOptions;
@@ -412,10 +418,12 @@ void serve_destroy(gb_server *srv);
  * limit; other precisions return GB_EINVAL.  The CG loop is always direct
  * launches polled from the host (opt->use_graph is ignored), the call
  * synchronises `stream`, and stats->solve_ms is host wall time.
- * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture begins.  All calls share the one array and the solver scalars are
- * reset at the start of every call; two calls whose work overlaps on the GPU
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing once the library's module is
+ * loaded there); the first call on a device may be what loads the module,
+ * which reserves the array, so make that first call before any stream capture
+ * begins.  All calls share the one array and the solver scalars are reset at
+ * the start of every call; two calls whose work overlaps on the GPU
  * (different streams or threads) race on that array and give wrong results. */
 int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
                       void *stream, PcgStats *stats);

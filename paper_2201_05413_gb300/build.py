@@ -13,12 +13,16 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+# GBPCG_NVCC_DEFINES: extra -D options for experiments (a build of its own
+# objects, linked into the same library path)
+DEFINES = os.environ.get("GBPCG_NVCC_DEFINES", "").split()
+OUT_DIR = os.path.join(HERE, "_build" + ("_" + "_".join(d.lstrip("-D").replace("=", "") for d in DEFINES)
+                                         if DEFINES else ""))
 LIB = os.path.join(HERE, "libgbpcg.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "-I", os.path.join(ROOT, "include")] + ARCH
+         "-I", os.path.join(ROOT, "include")] + ARCH + DEFINES
 
 
 def _deps(src):
@@ -50,7 +54,7 @@ def build(verbose: bool = False) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(_compile, srcs))
-    if _stale(LIB, objs):
+    if _stale(LIB, objs) or DEFINES:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)

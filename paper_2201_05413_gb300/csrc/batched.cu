@@ -167,10 +167,13 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
     return GB_OK;
 }
 
-// One launch of the persistent kernel over the systems in `list` (their
+// One launch of a persistent kernel over the systems in `list` (their
 // initial residuals already formed): fp64 CG for fp64 batches, fp32 correction
-// solves in fp64 refinement otherwise.
-static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions &o, bool ir, cudaStream_t st) {
+// solves in fp64 refinement otherwise.  tier 1: one block per system
+// (k_bpersist); tier 2: one cluster of CLUSTER_CS blocks per system
+// (k_bcluster), as many clusters as the SMs hold side by side.
+static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions &o, bool ir, cudaStream_t st,
+                       int tier = 1) {
     int *d_list = nullptr, *d_next = nullptr;
     GB_TRY(b.take(&d_list, list.size()));
     GB_TRY(b.take(&d_next, 1));
@@ -181,10 +184,16 @@ static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions 
     po.inner_tol = ir ? std::min(o.inner_tol, 1e-4) : 0.0;
     po.maxit = o.max_iter;
     po.max_outer = ir ? o.max_outer : 50;
-    const int grid = (int)std::min<size_t>(list.size(), (size_t)num_sms() * 2);
     ::gb::count_launches(1);
-    if (ir) k_bpersist<float><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
-    else k_bpersist<double><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+    if (tier == 2) {
+        const int nclu = (int)std::min<size_t>(list.size(), (size_t)std::max(1, num_sms() / CLUSTER_CS));
+        if (ir) k_bcluster<float><<<nclu * CLUSTER_CS, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+        else k_bcluster<double><<<nclu * CLUSTER_CS, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+    } else {
+        const int grid = (int)std::min<size_t>(list.size(), (size_t)num_sms() * 2);
+        if (ir) k_bpersist<float><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+        else k_bpersist<double><<<grid, PNT, 0, st>>>(b.d_sys, d_list, (int)list.size(), d_next, po);
+    }
     GB_CHECK_CUDA(cudaGetLastError());
     return GB_OK;
 }
@@ -235,13 +244,22 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     std::vector<long long> restarts(nsys, 0);
     std::vector<long long> fallback_its(nsys, 0);
     // small systems: solved whole by the persistent CTA-local kernel, one
-    // launch for all of them; the loops below then find them converged (or
-    // take over the columns it left above tol)
-    std::vector<int> plist;
-    for (int s = 0; s < nsys; ++s)
-        if (!o.persist_off && persist_eligible(A[s]->n, k[s])) plist.push_back(s);
+    // launch for all of them; medium ones by the cluster kernel, one launch
+    // for all of them; the loops below then find them converged (or take
+    // over the columns they left above tol)
+    std::vector<int> plist, clist;
+    for (int s = 0; s < nsys; ++s) {
+        const int tier = o.persist_off == 1 ? 0 : persist_tier(A[s]->n, k[s]);
+        if (tier == 1) plist.push_back(s);
+        else if (tier == 2 && o.persist_off != 2) clist.push_back(s);
+    }
+    if (!clist.empty()) GB_TRY(run_persist(b, clist, o, ir, st, 2));
+    for (int s : clist) plist.push_back(s);
     if (!plist.empty()) {
-        GB_TRY(run_persist(b, plist, o, ir, st));
+        if ((int)plist.size() > (int)clist.size()) {
+            std::vector<int> small(plist.begin(), plist.end() - clist.size());
+            GB_TRY(run_persist(b, small, o, ir, st, 1));
+        }
         GB_TRY(pull_cols(b, hc, st));
         std::vector<BSys> hs(nsys);
         GB_CHECK_CUDA(cudaMemcpyAsync(hs.data(), b.d_sys, sizeof(BSys) * nsys, cudaMemcpyDeviceToHost, st));

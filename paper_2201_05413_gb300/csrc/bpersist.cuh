@@ -18,22 +18,49 @@
 // and x += ||r|| d stay in fp64; the correction d solves A d = r / ||r|| by fp32
 // CG (fp32 values and vectors) to the relative residual inner_tol.
 //
-// Thread layout: kp = the power of two >= k; thread t owns column t mod kp (idle
-// when >= k) of rows t / kp, t / kp + PNT / kp, ...; per-column sums run an xor
-// tree over the lanes of a column and then the warps in order.
+// Thread layout: kp = the power of two >= k; thread t of the group owns
+// column t mod kp (idle when >= k) of rows t / kp, t / kp + GN / kp, ...;
+// per-column sums run an xor tree over the lanes of a column and then the
+// warps in order.
+//
+// The phases are written once for a "group" of threads that solves one
+// system together:
+//   CtaGroup      one block (k_bpersist, small systems: n kp <= 2^15);
+//   ClusterGroup  the CS = 8 blocks of a thread-block cluster (k_bcluster,
+//                 medium systems: 2^15 < n kp <= 2^19).  Each block reduces
+//                 its partial sums itself, publishes them in its shared
+//                 memory, and after a cluster barrier every block reads the 8
+//                 partials through distributed shared memory in rank order,
+//                 so all blocks hold the same sums and take the same
+//                 decisions.  The barrier (barrier.cluster, release/acquire)
+//                 also orders the blocks' global writes of the vectors other
+//                 blocks gather next (p, x); those gathers read L2 (ld.cg).
+//                 The blocks of a cluster are co-scheduled by the hardware,
+//                 so its barrier is not a spin on memory.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "bsys.cuh"
 
 namespace gb {
 
 constexpr int PNT = 512;                         // threads per block
-constexpr int64_t PERSIST_MAX_ELEMS = 1 << 15;   // n * kp of a system this kernel takes
+constexpr int64_t PERSIST_MAX_ELEMS = 1 << 15;   // n * kp of a system the CTA-local kernel takes
+constexpr int CLUSTER_CS = 8;                    // blocks per cluster (the portable maximum)
+constexpr int64_t CLUSTER_MAX_ELEMS = 1 << 19;   // n * kp of a system the cluster kernel takes
 
 struct PersistOpts {
     long long maxit;    // iterations per column (fp64) / inner iterations per outer step (fp32)
     double tol;         // Eq. (2) threshold
     double inner_tol;   // fp32 inner relative residual
     int max_outer;      // refinement steps (fp32) / true-residual restarts (fp64)
+};
+
+// Shared-memory scratch of the group's reductions.
+struct GrpSmem {
+    double red[PNT / 32][32];  // warp partials
+    double xs[2][32];          // this block's per-column sums, published to the cluster (two phases)
+    int ph;                    // phase of the next cluster exchange
 };
 
 // Per-column block sum; every thread passes its value, threads j < k read
@@ -51,6 +78,45 @@ __device__ __forceinline__ void p_colsum(double v, int kp, double (*red)[32], do
     __syncthreads();
 }
 
+struct CtaGroup {
+    static constexpr int GN = PNT;  // threads of the group
+    static __device__ __forceinline__ int gtid() { return threadIdx.x; }
+    static __device__ __forceinline__ bool leader() { return true; }
+    // the group's global writes before the call are seen by its reads after it
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    template <class T> static __device__ __forceinline__ T ldv(const T *p) { return *p; }
+    static __device__ __forceinline__ void colsum(double v, int kp, GrpSmem &g, double *out) {
+        p_colsum(v, kp, g.red, out);
+    }
+};
+
+struct ClusterGroup {
+    static constexpr int GN = CLUSTER_CS * PNT;
+    static __device__ __forceinline__ int rank() { return (int)cooperative_groups::this_cluster().block_rank(); }
+    static __device__ __forceinline__ int gtid() { return rank() * PNT + (int)threadIdx.x; }
+    static __device__ __forceinline__ bool leader() { return rank() == 0; }
+    static __device__ __forceinline__ void sync() { cooperative_groups::this_cluster().sync(); }
+    template <class T> static __device__ __forceinline__ T ldv(const T *p) { return __ldcg(p); }
+    // block sums, published in xs[ph]; after the cluster barrier each block
+    // adds the CS blocks' sums in rank order.  The next exchange writes the
+    // other phase, and a block can only reach the one after that once every
+    // block has passed the barrier of the next one, i.e. finished reading.
+    static __device__ __forceinline__ void colsum(double v, int kp, GrpSmem &g, double *out) {
+        const int ph = g.ph;
+        p_colsum(v, kp, g.red, g.xs[ph]);
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        cl.sync();
+        if (threadIdx.x < (unsigned)kp) {
+            double s = 0.0;
+            for (int r = 0; r < CLUSTER_CS; ++r) s += cl.map_shared_rank(&g.xs[ph][0], r)[threadIdx.x];
+            out[threadIdx.x] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) g.ph = ph ^ 1;
+        __syncthreads();
+    }
+};
+
 struct PState {  // per-column scalars of the running recurrence (shared memory)
     double alpha[32], beta[32], rho[32], thresh[32], rr[32], scale[32], t0[32], t1[32];
     long long it[32];
@@ -61,13 +127,13 @@ struct PState {  // per-column scalars of the running recurrence (shared memory)
 // q = A p for the columns of this thread, partial p.q; TV values, TX vectors.
 // The vectors are rewritten inside this kernel, so they are read with plain
 // (coherent) loads: no __restrict__ / read-only-cache loads on them.
-template <class TV, class TX>
+template <class Grp, class TV, class TX>
 __device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict__ val, const TX *P, TX *Q,
                                          int64_t n, int k, int kp, int j, bool on) {
     double pq = 0.0;
     if (!on) return pq;
     const int C = A.C;
-    for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+    for (int64_t r = Grp::gtid() / kp; r < n; r += Grp::GN / kp) {
         const int64_t c = r / C;
         const int L = A.row_len[r];
         const int64_t base = A.chunk_ptr[c] + (r - c * C);
@@ -79,8 +145,8 @@ __device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict
                       c3 = __ldg(A.col + e + 3 * C);
             const TX v0 = (TX)ld_val(val + e), v1 = (TX)ld_val(val + e + C), v2 = (TX)ld_val(val + e + 2 * C),
                      v3 = (TX)ld_val(val + e + 3 * C);
-            const TX p0 = P[(int64_t)c0 * k + j], p1 = P[(int64_t)c1 * k + j], p2 = P[(int64_t)c2 * k + j],
-                     p3 = P[(int64_t)c3 * k + j];
+            const TX p0 = Grp::ldv(P + (int64_t)c0 * k + j), p1 = Grp::ldv(P + (int64_t)c1 * k + j),
+                     p2 = Grp::ldv(P + (int64_t)c2 * k + j), p3 = Grp::ldv(P + (int64_t)c3 * k + j);
             acc += v0 * p0;
             acc += v1 * p1;
             acc += v2 * p2;
@@ -88,7 +154,7 @@ __device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict
         }
         for (; s < L; ++s) {
             const int64_t e = base + (int64_t)s * C;
-            acc += (TX)ld_val(val + e) * P[(int64_t)__ldg(A.col + e) * k + j];
+            acc += (TX)ld_val(val + e) * Grp::ldv(P + (int64_t)__ldg(A.col + e) * k + j);
         }
         Q[r * k + j] = acc;
         pq += (double)(P[r * k + j] * acc);
@@ -99,21 +165,22 @@ __device__ __forceinline__ double p_spmv(const SellView &A, const TV *__restrict
 // Runs CG on (X, R, P, Q) for the columns with st.run[j] set, stopping each at
 // ||R_j||^2 <= st.thresh[j], at st.it[j] == maxit, or on breakdown.  R holds the
 // starting residual; X is updated in place.
-template <class TV, class TX, class TD>
+template <class Grp, class TV, class TX, class TD>
 __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__restrict__ dinv, TX *X, TX *R, TX *P,
-                     TX *Q, int64_t n, int k, int kp, long long maxit, PState &st, double (*red)[32]) {
+                     TX *Q, int64_t n, int k, int kp, long long maxit, PState &st, GrpSmem &gs) {
     const int j = threadIdx.x % kp;
+    const int64_t row0 = Grp::gtid() / kp, rstep = Grp::GN / kp;
     // start: P = D^-1 R, rho = R.D^-1 R
     {
         const bool on = j < k && st.run[j];
         double rz = 0.0;
         if (on)
-            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+            for (int64_t r = row0; r < n; r += rstep) {
                 const TX z = (TX)dinv[r] * R[r * k + j];
                 P[r * k + j] = z;
                 rz += (double)(R[r * k + j] * z);
             }
-        p_colsum(rz, kp, red, st.t0);
+        Grp::colsum(rz, kp, gs, st.t0);  // (in a cluster: also publishes P before the first gathers)
         if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
             const double t = st.t0[threadIdx.x];
             st.rho[threadIdx.x] = t;
@@ -127,8 +194,8 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
         if (!any) break;
         const bool on = j < k && st.run[j];
         // q = A p, alpha = rho / p.q
-        const double pq = p_spmv<TV, TX>(A, val, P, Q, n, k, kp, j, on);
-        p_colsum(pq, kp, red, st.t0);
+        const double pq = p_spmv<Grp, TV, TX>(A, val, P, Q, n, k, kp, j, on);
+        Grp::colsum(pq, kp, gs, st.t0);
         if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
             const double t = st.t0[threadIdx.x];
             if (!(t > 0.0) || !isfinite(t)) { st.run[threadIdx.x] = 0; st.status[threadIdx.x] = ST_BREAK; }
@@ -141,8 +208,8 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
         if (on2) {
             const TX a = (TX)st.alpha[j];
             constexpr int U = 4;  // rows in flight per thread
-            const int64_t step = PNT / kp;
-            for (int64_t r0 = threadIdx.x / kp; r0 < n; r0 += U * step) {
+            const int64_t step = rstep;
+            for (int64_t r0 = row0; r0 < n; r0 += U * step) {
                 TX xv[U], pv[U], rv[U], qv[U], dv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -166,8 +233,8 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
                 }
             }
         }
-        p_colsum(rz, kp, red, st.t0);
-        p_colsum(rr, kp, red, st.t1);
+        Grp::colsum(rz, kp, gs, st.t0);
+        Grp::colsum(rr, kp, gs, st.t1);
         if (threadIdx.x < (unsigned)k && st.run[threadIdx.x]) {
             const int q = threadIdx.x;
             st.it[q] += 1;
@@ -183,8 +250,8 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
         if (on3) {
             const TX b = (TX)st.beta[j];
             constexpr int U = 4;
-            const int64_t step = PNT / kp;
-            for (int64_t r0 = threadIdx.x / kp; r0 < n; r0 += U * step) {
+            const int64_t step = rstep;
+            for (int64_t r0 = row0; r0 < n; r0 += U * step) {
                 TX pv[U], rv[U], dv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -198,39 +265,41 @@ __device__ void p_cg(const SellView &A, const TV *__restrict__ val, const TD *__
                 }
             }
         }
-        __syncthreads();
+        Grp::sync();  // the new P before the next gathers
     }
 }
 
 // R64 = B64 - A X64 in fp64 for the columns in `sel`; ||R64_j||^2 into st.rr.
-static __device__ void p_resid(const BSys &S, int64_t n, int k, int kp, const int *sel, PState &st, double (*red)[32]) {
+template <class Grp>
+static __device__ void p_resid(const BSys &S, int64_t n, int k, int kp, const int *sel, PState &st, GrpSmem &gs) {
     const int j = threadIdx.x % kp;
     double rr = 0.0;
     if (j < k && sel[j]) {
         const SellView &A = S.A;
         const int C = A.C;
-        for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+        for (int64_t r = Grp::gtid() / kp; r < n; r += Grp::GN / kp) {
             const int64_t c = r / C;
             const int L = A.row_len[r];
             const int64_t base = A.chunk_ptr[c] + (r - c * C);
             double acc = 0.0;
             for (int s = 0; s < L; ++s) {
                 const int64_t e = base + (int64_t)s * C;
-                acc += ld_val(A.val + e) * S.X64[(int64_t)__ldg(A.col + e) * k + j];
+                acc += ld_val(A.val + e) * Grp::ldv(S.X64 + (int64_t)__ldg(A.col + e) * k + j);
             }
             const double ri = S.B64[r * k + j] - acc;
             S.R64[r * k + j] = ri;
             rr += ri * ri;
         }
     }
-    p_colsum(rr, kp, red, st.t1);
+    Grp::colsum(rr, kp, gs, st.t1);
     if (threadIdx.x < (unsigned)k && sel[threadIdx.x]) st.rr[threadIdx.x] = st.t1[threadIdx.x];
     __syncthreads();
 }
 
 // One system, fp64 recurrences.  Entry state (from the batch's initial
 // residual kernel): R64 = B - A X0, c.rr, c.bb, c.thresh.
-static __device__ void p_solve_f64(BSys &S, const PersistOpts &o, PState &st, double (*red)[32], int *sel) {
+template <class Grp>
+static __device__ void p_solve_f64(BSys &S, const PersistOpts &o, PState &st, GrpSmem &gs, int *sel) {
     const int64_t n = S.A.n;
     const int k = S.k;
     int kp = 1;
@@ -260,9 +329,9 @@ static __device__ void p_solve_f64(BSys &S, const PersistOpts &o, PState &st, do
         int any = 0;
         for (int q = 0; q < k; ++q) any |= sel[q];
         if (!any) break;
-        p_cg<double, double, double>(S.A, S.A.val, S.A.dinv, S.X64, S.R64, (double *)S.P, (double *)S.Q, n, k, kp,
-                                     o.maxit, st, red);
-        p_resid(S, n, k, kp, sel, st, red);  // true residual of the columns just run
+        p_cg<Grp, double, double, double>(S.A, S.A.val, S.A.dinv, S.X64, S.R64, (double *)S.P, (double *)S.Q, n, k,
+                                          kp, o.maxit, st, gs);
+        p_resid<Grp>(S, n, k, kp, sel, st, gs);  // true residual of the columns just run
         if (round == o.max_outer && threadIdx.x < (unsigned)k && sel[threadIdx.x] &&
             st.rr[threadIdx.x] > st.thresh[threadIdx.x] && st.status[threadIdx.x] == ST_CONV)
             st.status[threadIdx.x] = ST_MAXIT;
@@ -271,7 +340,8 @@ static __device__ void p_solve_f64(BSys &S, const PersistOpts &o, PState &st, do
 }
 
 // One system, fp32 correction solves inside fp64 refinement.
-static __device__ void p_solve_ir(BSys &S, const PersistOpts &o, PState &st, double (*red)[32], int *sel) {
+template <class Grp>
+static __device__ void p_solve_ir(BSys &S, const PersistOpts &o, PState &st, GrpSmem &gs, int *sel) {
     const int64_t n = S.A.n;
     const int k = S.k;
     int kp = 1;
@@ -304,38 +374,55 @@ static __device__ void p_solve_ir(BSys &S, const PersistOpts &o, PState &st, dou
         if (!any) break;
         if (j < k && sel[j]) {
             const double sc = 1.0 / st.scale[j];
-            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) {
+            for (int64_t r = Grp::gtid() / kp; r < n; r += Grp::GN / kp) {
                 R[r * k + j] = (float)(sc * S.R64[r * k + j]);
                 D[r * k + j] = 0.0f;
             }
         }
         if (threadIdx.x < 32) st.it[threadIdx.x] = 0;
         __syncthreads();
-        p_cg<float, float, float>(S.A, S.A.val32, S.A.dinv32, D, R, P, Q, n, k, kp, o.maxit, st, red);
+        p_cg<Grp, float, float, float>(S.A, S.A.val32, S.A.dinv32, D, R, P, Q, n, k, kp, o.maxit, st, gs);
         long long mx = 0;
         for (int q = 0; q < k; ++q) if (sel[q]) mx = max(mx, st.it[q]);
         inner_total += mx;
         // x += ||r|| d in fp64, then the true residual
         if (j < k && sel[j]) {
             const double sc = st.scale[j];
-            for (int64_t r = threadIdx.x / kp; r < n; r += PNT / kp) S.X64[r * k + j] += sc * (double)D[r * k + j];
+            for (int64_t r = Grp::gtid() / kp; r < n; r += Grp::GN / kp) S.X64[r * k + j] += sc * (double)D[r * k + j];
         }
-        __syncthreads();
-        p_resid(S, n, k, kp, sel, st, red);
+        Grp::sync();  // the new X64 before p_resid gathers it
+        p_resid<Grp>(S, n, k, kp, sel, st, gs);
     }
     if (threadIdx.x < (unsigned)k) {
         const int q = threadIdx.x;
         st.status[q] = (S.c.bb[q] == 0.0 || st.rr[q] <= S.c.thresh[q]) ? ST_CONV : ST_MAXIT;
         st.it[q] = inner_total;
     }
-    if (threadIdx.x == 0) S.outer = outer;
+    if (threadIdx.x == 0 && Grp::leader()) S.outer = outer;
+    __syncthreads();
+}
+
+// The column state a finished system leaves for the host, as the batched
+// loop leaves it (written by the group's leader block).
+template <class Grp>
+static __device__ void p_publish(BSys &S, const PState &st) {
+    if (Grp::leader()) {
+        if (threadIdx.x < (unsigned)S.k) {
+            const int q = threadIdx.x;
+            S.c.rr[q] = st.rr[q];
+            S.c.status[q] = st.status[q];
+            S.c.it[q] = st.it[q];
+            S.c.done[q] = 1;
+        }
+        if (threadIdx.x == 0) S.active = 0;
+    }
     __syncthreads();
 }
 
 template <class TX>
 __global__ void __launch_bounds__(PNT) k_bpersist(BSys *sys, const int *list, int nlist, int *next, PersistOpts o) {
     __shared__ PState st;
-    __shared__ double red[PNT / 32][32];
+    __shared__ GrpSmem gs;
     __shared__ int sel[32];
     __shared__ int idx;
     for (;;) {
@@ -345,26 +432,46 @@ __global__ void __launch_bounds__(PNT) k_bpersist(BSys *sys, const int *list, in
         __syncthreads();
         if (i >= nlist) break;
         BSys &S = sys[list[i]];
-        if (sizeof(TX) == 8) p_solve_f64(S, o, st, red, sel);
-        else p_solve_ir(S, o, st, red, sel);
-        // column state for the host, as the batched loop leaves it
-        if (threadIdx.x < (unsigned)S.k) {
-            const int q = threadIdx.x;
-            S.c.rr[q] = st.rr[q];
-            S.c.status[q] = st.status[q];
-            S.c.it[q] = st.it[q];
-            S.c.done[q] = 1;
-        }
-        if (threadIdx.x == 0) S.active = 0;
-        __syncthreads();
+        if (sizeof(TX) == 8) p_solve_f64<CtaGroup>(S, o, st, gs, sel);
+        else p_solve_ir<CtaGroup>(S, o, st, gs, sel);
+        p_publish<CtaGroup>(S, st);
     }
 }
 
-// Whether a system goes to the persistent kernel.
-inline bool persist_eligible(int64_t n, int k) {
+// The cluster tier: each cluster of CLUSTER_CS blocks takes the next system
+// of the list (the rank-0 block draws it, the others read it through
+// distributed shared memory) and solves it whole.
+template <class TX>
+__global__ void __cluster_dims__(CLUSTER_CS, 1, 1) __launch_bounds__(PNT)
+    k_bcluster(BSys *sys, const int *list, int nlist, int *next, PersistOpts o) {
+    __shared__ PState st;
+    __shared__ GrpSmem gs;
+    __shared__ int sel[32];
+    __shared__ int idx;
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    if (threadIdx.x == 0) gs.ph = 0;
+    for (;;) {
+        if (threadIdx.x == 0 && cl.block_rank() == 0) idx = atomicAdd(next, 1);
+        cl.sync();
+        const int i = *cl.map_shared_rank(&idx, 0);
+        cl.sync();  // every block has read idx before rank 0 draws again
+        if (i >= nlist) break;
+        BSys &S = sys[list[i]];
+        if (sizeof(TX) == 8) p_solve_f64<ClusterGroup>(S, o, st, gs, sel);
+        else p_solve_ir<ClusterGroup>(S, o, st, gs, sel);
+        p_publish<ClusterGroup>(S, st);
+    }
+}
+
+// Which persistent tier takes a system: 0 none (the multi-launch loop),
+// 1 CTA-local, 2 cluster.
+inline int persist_tier(int64_t n, int k) {
     int kp = 1;
     while (kp < k) kp <<= 1;
-    return n * kp <= PERSIST_MAX_ELEMS;
+    if (n * kp <= PERSIST_MAX_ELEMS) return 1;
+    if (n * kp <= CLUSTER_MAX_ELEMS) return 2;
+    return 0;
 }
+inline bool persist_eligible(int64_t n, int k) { return persist_tier(n, k) == 1; }
 
 }  // namespace gb

@@ -32,6 +32,10 @@ template <class TX, int K> struct BSlice {
 
 // Resident blocks per SM for width K: accumulators (K columns) + the gather
 // buffer + ~44 registers of addressing must fit 65536 / (NT x blocks).
+#ifndef GB_BSPMM_INTERLEAVE
+#define GB_BSPMM_INTERLEAVE 1
+#endif
+constexpr bool BSPMM_INTERLEAVE = GB_BSPMM_INTERLEAVE != 0;
 #ifndef GB_BSPMM_WIDE_GBUF
 #define GB_BSPMM_WIDE_GBUF 32
 #endif
@@ -49,12 +53,14 @@ template <class TX, int K> struct BspmmOcc {
     static constexpr int blocks = R <= 64 ? 4 : (R <= 84 ? 3 : 2);
 };
 
-// One warp's chunk range [c0, c1) of system S.  For each column-step of a
-// chunk the 32 rows are taken in G passes of R rows; in pass q lane l works on
-// row q R + l / G and columns (l mod G) VW .. +VW.  Returns the lane's
-// partial P.Q for its VW columns in dot[].
+// One warp's chunks c0, c0 + cs, ..., c0 + (nc - 1) cs of system S (cs = 1:
+// a contiguous range, streamed as one linear array; cs > 1: the chunks are
+// copied piece by piece, a stage never mixing two chunks' bytes in one copy).
+// For each column-step of a chunk the 32 rows are taken in G passes of R
+// rows; in pass q lane l works on row q R + l / G and columns (l mod G) VW ..
+// +VW.  Returns the lane's partial P.Q for its VW columns in dot[].
 template <class TX, class TV, int K>
-__device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int64_t c1, Tma2Ring<TV> &sm,
+__device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int64_t nc, int cs, Tma2Ring<TV> &sm,
                                                   uint64_t *bars, bool *timed_out, TX (&dot)[BSlice<TX, K>::VW]) {
     constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW, R = BSlice<TX, K>::R;
@@ -72,24 +78,55 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
     TX *__restrict__ Q = (TX *)S.Q;
 #pragma unroll
     for (int u = 0; u < VW; ++u) dot[u] = TX(0);
-    if (c0 >= c1) return;
-    const int64_t e0 = __ldg(A.chunk_ptr + c0), e1 = __ldg(A.chunk_ptr + c1);
-    const int64_t nsteps = (e1 - e0) >> 5;
+    if (nc <= 0) return;
+    const int64_t e0 = __ldg(A.chunk_ptr + c0);
+    int64_t nsteps;
+    if (cs == 1) {
+        nsteps = (__ldg(A.chunk_ptr + c0 + nc) - e0) >> 5;
+    } else {
+        int64_t t = 0;
+        for (int64_t i = lane; i < nc; i += 32) t += __ldg(A.chunk_w + c0 + i * cs);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+        nsteps = t;
+    }
     const int64_t nstages = (nsteps + SJ - 1) / SJ;
     uint64_t pol = 0;
     if (GB_TMA2_EVICT_FIRST && lane == 0) pol = l2_policy_evict_first();
     int64_t issued = 0;
+    int64_t ic = 0, ioff = 0;  // issue cursor (lane 0, cs > 1): chunk index, steps of it already issued
     auto issue = [&](int64_t st) {
         issued = st + 1;
         if (lane == 0) {
             const int b = (int)(st % NB);
             const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
-            const int64_t off = e0 + st * SJ * 32;
-            const uint32_t bc = (uint32_t)(sj * 32 * sizeof(int32_t));
-            const uint32_t bv = (uint32_t)(sj * 32 * sizeof(TV));
-            mbar_expect_tx(&bars[b], bc + bv);
-            bulk_g2s_pol(sm.col[b], A.col + off, bc, &bars[b], pol);
-            bulk_g2s_pol(sm.val[b], val + off, bv, &bars[b], pol);
+            mbar_expect_tx(&bars[b], (uint32_t)(sj * 32 * (sizeof(int32_t) + sizeof(TV))));
+            if (cs == 1) {
+                const int64_t off = e0 + st * SJ * 32;
+                bulk_g2s_pol(sm.col[b], A.col + off, (uint32_t)(sj * 32 * sizeof(int32_t)), &bars[b], pol);
+                bulk_g2s_pol(sm.val[b], val + off, (uint32_t)(sj * 32 * sizeof(TV)), &bars[b], pol);
+            } else {
+                // the stage's sj steps from the chunks at the cursor, one piece per chunk
+                int filled = 0;
+                while (filled < sj && ic < nc) {
+                    const int64_t c = c0 + ic * cs;
+                    const int64_t w = __ldg(A.chunk_w + c);
+                    const int take = (int)min((int64_t)(sj - filled), w - ioff);
+                    if (take > 0) {
+                        const int64_t off = __ldg(A.chunk_ptr + c) + ioff * 32;
+                        bulk_g2s_pol(sm.col[b] + filled * 32, A.col + off, (uint32_t)(take * 32 * sizeof(int32_t)),
+                                     &bars[b], pol);
+                        bulk_g2s_pol(sm.val[b] + filled * 32, val + off, (uint32_t)(take * 32 * sizeof(TV)),
+                                     &bars[b], pol);
+                        filled += take;
+                        ioff += take;
+                    }
+                    if (ioff >= w) {
+                        ++ic;
+                        ioff = 0;
+                    }
+                }
+            }
         }
     };
     for (int64_t st = 0; st < nstages && st < NB; ++st) issue(st);
@@ -118,10 +155,12 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
         }
     };
 
-    int64_t cb = c0;
+    // consume cursor: chunk tb + ci of the warp's list (widths of tb .. tb + 31
+    // held one per lane), `left` steps of it still to come
+    int64_t tb = 0;
     int ci = -1, left = 0;
-    int wv = (cb + lane < c1) ? __ldg(A.chunk_w + cb + lane) : 0;
-    int64_t rbase = c0 * 32 - 32;  // first row of the current chunk
+    int wv = (lane < nc) ? __ldg(A.chunk_w + c0 + (int64_t)lane * cs) : 0;
+    int64_t rbase = 0;  // first row of the current chunk
     TX acc[G][VW];
 #pragma unroll
     for (int q = 0; q < G; ++q)
@@ -130,13 +169,13 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
     auto next_chunk = [&]() {
         do {
             if (++ci == 32) {
-                cb += 32;
+                tb += 32;
                 ci = 0;
-                wv = (cb + lane < c1) ? __ldg(A.chunk_w + cb + lane) : 0;
+                wv = (tb + lane < nc) ? __ldg(A.chunk_w + c0 + (tb + lane) * cs) : 0;
             }
             left = __shfl_sync(FULL, wv, ci);
-            rbase += 32;
-            if (left == 0 && cb + ci < c1) {  // an all-empty chunk: its rows of Q are zero
+            rbase = (c0 + (tb + ci) * cs) * 32;
+            if (left == 0 && tb + ci < nc) {  // an all-empty chunk: its rows of Q are zero
                 TX z[VW];
 #pragma unroll
                 for (int u = 0; u < VW; ++u) z[u] = TX(0);
@@ -144,7 +183,7 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
                 for (int q = 0; q < G; ++q)
                     if (rbase + q * R + sub < A.n) stq(rbase + q * R + sub, z);
             }
-        } while (left == 0 && cb + ci < c1);
+        } while (left == 0 && tb + ci < nc);
     };
     next_chunk();
     auto flush = [&]() {  // chunk complete (warp-uniform)
@@ -277,12 +316,24 @@ __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))
     const int64_t cpu = S.rows_per_unit >> 5;  // chunks per unit
     const int64_t uc0 = (int64_t)(u - S.unit0) * cpu;
     const int64_t uc1 = min(S.A.nchunks, uc0 + cpu);
-    const int64_t cpw = (cpu + TMA_WARPS - 1) / TMA_WARPS;
-    const int64_t wc0 = min(uc1, uc0 + warp * cpw), wc1 = min(uc1, wc0 + cpw);
     bool timed_out = false;
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW;
     TX dot[VW];
-    bspmm_warp_stream<TX, TV, K>(S, wc0, wc1, bufs[warp], &bars[NB * warp], &timed_out, dot);
+    if (BSPMM_INTERLEAVE && G > 1 && sizeof(TX) == 4) {
+        // fp32 rows of wide P blocks (G lanes per row): warp w takes chunks
+        // uc0 + w, uc0 + w + 8, ..., so the block's 8 warps work on
+        // neighbouring chunks (one sorting window of 256 rows at a time) and
+        // gather overlapping sets of P rows (2D P2 1024^2, k = 32: 0.870
+        // against 0.896 ms per launch; fp64, bound by its FMA rate, keeps the
+        // contiguous ranges: 0.85 against 0.94 ms at k = 8)
+        const int64_t w0 = uc0 + warp;
+        const int64_t nc = w0 < uc1 ? (uc1 - w0 + TMA_WARPS - 1) / TMA_WARPS : 0;
+        bspmm_warp_stream<TX, TV, K>(S, w0, nc, TMA_WARPS, bufs[warp], &bars[NB * warp], &timed_out, dot);
+    } else {
+        const int64_t cpw = (cpu + TMA_WARPS - 1) / TMA_WARPS;
+        const int64_t wc0 = min(uc1, uc0 + warp * cpw), wc1 = min(uc1, wc0 + cpw);
+        bspmm_warp_stream<TX, TV, K>(S, wc0, wc1 - wc0, 1, bufs[warp], &bars[NB * warp], &timed_out, dot);
+    }
     if (timed_out && lane == 0) atomicExch(&G_->err, 1);
     // per-column unit sums in a fixed order: the lanes of a column inside the
     // warp (xor tree over the lane bits above the slice), then warps in order

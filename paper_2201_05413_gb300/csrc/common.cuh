@@ -60,6 +60,8 @@ void set_capturing(bool on);
 // ---------------------------------------------------------------- memory --
 // Allocations go through the caller's allocator, or cudaMalloc/cudaFree when
 // none was given (the stream is passed to the caller's allocator only).
+void count_device_alloc();  // every device allocation Mem makes (gbpcg_device_allocations)
+
 struct Mem {
     gb_allocator a{};
     bool has = false;
@@ -74,6 +76,7 @@ struct Mem {
         if (has) {
             *p = a.alloc(a.ctx, bytes, (void *)s);
             if (!*p) { set_error("allocator returned NULL for %zu bytes", bytes); return GB_ENOMEM; }
+            count_device_alloc();
             return GB_OK;
         }
         cudaError_t e = cudaMalloc(p, bytes);
@@ -82,6 +85,7 @@ struct Mem {
             *p = nullptr;
             return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
         }
+        count_device_alloc();
         return GB_OK;
     }
     template <class T> int alloc_n(T **p, size_t n) { return alloc((void **)p, n * sizeof(T)); }

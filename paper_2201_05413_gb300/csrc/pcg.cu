@@ -1392,27 +1392,29 @@ constexpr size_t NOALLOC_BYTES = (size_t)5 * NOALLOC_MAX_N * sizeof(double) +
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 // Host code must not take the address of g_noalloc_scratch directly (that is
-// a host-side stand-in); the device address is looked up once per device.
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[128] = {};
-
+// a host-side stand-in).  The device address is looked up on every call, on
+// the current device: a cached address could outlive the module it points
+// into (a device reset or context teardown reloads it elsewhere).
 static int noalloc_scratch(unsigned char **out) {
-    int dev = 0;
-    GB_CHECK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) { set_error("pcg_solve_noalloc: device %d out of range", dev); return GB_EINVAL; }
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("pcg_solve_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return GB_ECUDA;
-        }
-        g_noalloc_ptr[dev] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("pcg_solve_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return GB_ECUDA;
     }
-    *out = (unsigned char *)g_noalloc_ptr[dev];
+    *out = (unsigned char *)p;
     return GB_OK;
 }
+
+// A Work whose buffers are views into the static array: its fields are
+// cleared on every way out of scope, before ~Work would release them.
+struct NoallocWork {
+    Work w;
+    ~NoallocWork() {
+        w.x = w.r = w.p = w.q = w.b = w.z = w.partials = nullptr;
+        w.S = nullptr;
+    }
+};
 }  // namespace gb
 
 extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
@@ -1441,7 +1443,8 @@ extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_
     unsigned char *base = nullptr;
     GB_TRY(noalloc_scratch(&base));
     cudaStream_t st = (cudaStream_t)stream;
-    Work w;  // views into the static array; nothing here is released
+    NoallocWork nw;  // views into the static array; nothing here is released
+    Work &w = nw.w;
     w.mem = Mem(nullptr, st);
     double *vec = (double *)base;
     w.x = vec;
@@ -1467,8 +1470,6 @@ extern "C" int pcg_solve_noalloc(const gb_sell *A, const double *d_b, double *d_
         stats->kernel_launches += 3;
     }
     stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    w.x = w.r = w.p = w.q = w.b = w.partials = nullptr;
-    w.S = nullptr;
     if (rc != GB_OK) return rc;
     if (stats->status != GB_OK) {
         set_error("pcg_solve_noalloc: %s after %lld iterations (relres %.3e)",

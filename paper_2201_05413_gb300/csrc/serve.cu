@@ -58,6 +58,7 @@ struct Slot {
     int64_t n = 0;
     int k = 1, kw = 1;
     bool ru = true;
+    int ptier = 0;  // persistent tier solving it (1 one block, 2 one cluster), 0 = the lock-step loop
     double *B64 = nullptr, *X64 = nullptr, *R64 = nullptr;
     void *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
     double *cd = nullptr;
@@ -237,16 +238,22 @@ static int grow(gb_server *s, T **p, size_t *cap, size_t need, cudaStream_t st) 
 }
 
 // Requests up to n * k2 <= 2^15 (k2: the power of two >= k) are solved by one
-// block each of k_bpersist: a block works through its request at one SM's
-// pace, which for such sizes beats advancing in lock-step with the largest
-// resident requests.
+// block each of k_bpersist, and requests up to n * k2 <= 2^19 by one 8-block
+// cluster each of k_bcluster: such a request works through its iterations at
+// the pace of its own SMs, which for these sizes beats advancing in lock-step
+// with the largest resident requests.  Returns the tier (0: lock-step loop).
 #ifndef GB_SERVE_PERSIST_LOG2
 #define GB_SERVE_PERSIST_LOG2 15
 #endif
-static bool serve_persist_eligible(int64_t n, int k, bool ru) {
+#ifndef GB_SERVE_CLUSTER
+#define GB_SERVE_CLUSTER 1
+#endif
+static int serve_persist_tier(int64_t n, int k, bool ru) {
     int kp = 1;
     while (kp < k) kp <<= 1;
-    return n * kp <= (ru ? ((int64_t)1 << GB_SERVE_PERSIST_LOG2) : PERSIST_MAX_ELEMS);
+    if (n * kp <= (ru ? ((int64_t)1 << GB_SERVE_PERSIST_LOG2) : PERSIST_MAX_ELEMS)) return 1;
+    if (GB_SERVE_CLUSTER && n * kp <= CLUSTER_MAX_ELEMS) return 2;
+    return 0;
 }
 
 // --------------------------------------------------------------- admit --
@@ -353,9 +360,11 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
         mask[j] = ru ? 2 : 1;
         target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
     }
-    if (serve_persist_eligible(L.n, L.k, ru)) {
-        // small or medium request: solved whole by one block of the next
-        // persistent launch (launch_persistent), not in the lock-step loop
+    L.ptier = serve_persist_tier(L.n, L.k, ru);
+    if (L.ptier) {
+        // small or medium request: solved whole by one block (or one cluster)
+        // of the next persistent launch (launch_persistent), not in the
+        // lock-step loop
         L.active = 0;
         L.state = SL_PWAIT;
         L.bytes = s->slot_bytes_acc;
@@ -527,11 +536,17 @@ static int service(gb_server *s, std::vector<Slot *> &sv) {
 }
 
 // ------------------------------------------------------ persistent lane --
-// One launch over every slot waiting for it (their initial residuals formed
-// at admission, which synchronised its stream).
+// One launch per tier over every slot of that tier waiting for it (their
+// initial residuals formed at admission, which synchronised its stream), each
+// on a stream of its own.
+static int launch_persistent_tier(gb_server *s, int tier);
 static int launch_persistent(gb_server *s) {
+    GB_TRY(launch_persistent_tier(s, 1));
+    return launch_persistent_tier(s, 2);
+}
+static int launch_persistent_tier(gb_server *s, int tier) {
     std::vector<Slot *> w;
-    for (auto &p : s->slots) if (p->state == SL_PWAIT) w.push_back(p.get());
+    for (auto &p : s->slots) if (p->state == SL_PWAIT && p->ptier == tier) w.push_back(p.get());
     if (w.empty()) return GB_OK;
     const bool ru = s->opt.precision != GB_F64;
     auto L = std::make_unique<gb_server::PLaunch>();
@@ -555,10 +570,16 @@ static int launch_persistent(gb_server *s) {
     po.inner_tol = 1e-4;
     po.maxit = std::min<long long>(s->opt.max_iter, maxit);
     po.max_outer = ru ? 30 : 50;
-    const int grid = std::min(m, num_sms() * 2);
     ::gb::count_launches(1);
-    if (ru) k_bpersist<float><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
-    else k_bpersist<double><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+    if (tier == 2) {
+        const int grid = std::min(m, std::max(1, num_sms() / CLUSTER_CS)) * CLUSTER_CS;
+        if (ru) k_bcluster<float><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+        else k_bcluster<double><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+    } else {
+        const int grid = std::min(m, num_sms() * 2);
+        if (ru) k_bpersist<float><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+        else k_bpersist<double><<<grid, PNT, 0, st>>>(L->d_tab, L->d_list, m, L->d_list + m, po);
+    }
     GB_CHECK_CUDA(cudaGetLastError());
     GB_CHECK_CUDA(cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming));
     GB_CHECK_CUDA(cudaEventRecord(L->done, st));

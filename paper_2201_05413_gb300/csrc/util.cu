@@ -16,6 +16,9 @@ void count_launches(int64_t k) {
 void set_capturing(bool on) { g_capturing = on; }
 long long launches_total() { return g_launches.load(); }
 
+static std::atomic<long long> g_dev_allocs{0};
+void count_device_alloc() { g_dev_allocs.fetch_add(1, std::memory_order_relaxed); }
+
 void set_error(const char *fmt, ...) {
     char buf[1024];
     va_list ap;
@@ -160,4 +163,5 @@ template int scan_exclusive<int64_t, int64_t>(const int64_t *, int64_t *, int64_
 
 extern "C" const char *gbpcg_last_error(void) { return gb::g_last_error.c_str(); }
 extern "C" int64_t gbpcg_kernel_launches(void) { return gb::launches_total(); }
+extern "C" int64_t gbpcg_device_allocations(void) { return gb::g_dev_allocs.load(); }
 extern "C" const char *gbpcg_version(void) { return "gbpcg 0.1 (sm_103a)"; }

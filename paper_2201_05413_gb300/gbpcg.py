@@ -127,6 +127,7 @@ _SIGS = {
     "gbpcg_last_error": (C.c_char_p, []),
     "gbpcg_version": (C.c_char_p, []),
     "gbpcg_kernel_launches": (C.c_int64, []),
+    "gbpcg_device_allocations": (C.c_int64, []),
     "fem_assemble": (C.c_int, [C.POINTER(gb_fem_spec), C.POINTER(gb_allocator), _P, C.POINTER(_P)]),
     "fem_system_info": (C.c_int, [_P, C.POINTER(gb_fem_info)]),
     "fem_dof_maps": (C.c_int, [_P, _P, _P, _P, _P]),

@@ -142,3 +142,44 @@ def test_boundary_data_from_host(P):
     s.assemble()
     u = s.eval_g(O.G_X2_Y2, None, 1, "free")[:, 0]  # P2 reproduces x^2 - y^2 exactly
     assert r["status"] == 0 and O.x_err(u, x[:, 0]) <= 1e-8
+
+
+MIX_TIERS = [  # one request per path: one block, one 8-block cluster (two), the lock-step loop
+    (2, 1, 40, 1, 1, 11, 2, O.G_HARMONIC),   # n k2 = 3042: one block
+    (2, 1, 200, 1, 1, 12, 2, O.G_HARMONIC),  # 79202: one cluster
+    (3, 2, 20, 0, 0, 0, 1, O.G_LINEAR),      # 59319: one cluster
+    (2, 1, 400, 1, 1, 13, 4, O.G_HARMONIC),  # 636804: lock-step loop
+]
+
+
+@pytest.mark.parametrize("prec", ["f32ru", "f64"])
+def test_medium_requests_through_cluster_lane(P, prec):
+    """Requests of every size class in one served mix: every column meets
+    Eq. 2 against the oracle's matrix, the cluster-solved requests are within
+    1e-8 of the oracle's solution, and each request served alone gives the
+    same bits."""
+    p = P.GB_F32_RU if prec == "f32ru" else P.GB_F64
+    mixed, stats = _serve(P, MIX_TIERS, precision=p, max_slots=8)
+    assert stats["completed"] == len(MIX_TIERS)
+    for i, ((r, x), req) in enumerate(zip(mixed, MIX_TIERS)):
+        assert r["status"] == 0, r
+        dim, deg, cells, jit, dm, seed = req[:6]
+        s = O.System(dim, deg, cells, jit, dm, seed).assemble()
+        rp, ci, v = s.k_ii()
+        B = s.lift(s.eval_g(req[7], _coef(i, req[6], req[7]), req[6], "bnd"))
+        for j in range(req[6]):
+            rel = np.linalg.norm(B[:, j] - O.spmv(rp, ci, v, x[:, j])) / np.linalg.norm(B[:, j])
+            assert rel <= 1.5 * TOL, (i, j, rel)
+            if i in (1, 2):
+                xo = O.pcg(rp, ci, v, B[:, j], tol=1e-13)[0]
+                assert O.x_err(xo, x[:, j]) <= 1e-8
+    for i, req in enumerate(MIX_TIERS):
+        srv = P.Server(precision=p, max_slots=1)
+        try:
+            t = srv.submit(*req[:6], k=req[6], gid=req[7], coef=_coef(i, req[6], req[7]))
+            (r, x), = srv.wait([t]).values()
+        finally:
+            srv.close()
+        rm, xm = mixed[i]
+        assert r["iterations"] == rm["iterations"], (i, r, rm)
+        assert np.array_equal(x, xm), i

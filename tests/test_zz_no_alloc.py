@@ -1,7 +1,9 @@
 """pcg_solve_noalloc: the fp64 solve for callers that cannot allocate device
 memory (its scratch is a fixed file-scope device array).  Called through the
 C ABI and compared with pcg_solve on the same system, twice in a row (the
-second call reuses the array the first one left behind).  This file sorts last
+second call reuses the array the first one left behind, and must leave the
+library's allocation count and the device's free memory unchanged), and from
+a nonzero starting iterate.  This file sorts last
 so that a run stopping at the first failure has run every other test."""
 import ctypes as C
 
@@ -29,7 +31,8 @@ def _noalloc(P, A, b, x0=None, **kw):
     from paper_2201_05413_gb300 import gbpcg as G
     from paper_2201_05413_gb300.api import _opts
     x = x0.clone() if x0 is not None else torch.full_like(b, float("nan"))
-    o = _opts(x0_zero=0 if x0 is not None else 1, **kw)
+    kw.setdefault("x0_zero", 0 if x0 is not None else 1)
+    o = _opts(**kw)
     st = G.PcgStats()
     rc = G.lib().pcg_solve_noalloc(A.handle, G.ptr(b), G.ptr(x), C.byref(o), G.stream_ptr(), C.byref(st))
     return rc, x, st
@@ -48,12 +51,38 @@ def test_noalloc_matches_pcg_solve_twice(P, spec):
     gid = 1 if spec[0] == 2 else 2
     b = d.lift(d.dirichlet(gid))[:, 0].contiguous()
     x_ref, st_ref = A.solve(b, tol=TOL, max_iter=200000)
-    for _ in range(2):
-        rc, x, st = _noalloc(P, A, b, tol=TOL, max_iter=200000)
-        assert rc == 0, P.gbpcg.lib().gbpcg_last_error()
+    import torch
+    L = P.gbpcg.lib()
+    x0 = torch.full_like(b, float("nan"))
+    for call in range(2):
+        # the second call must not allocate: the library's allocation count
+        # and the device's free memory are the same after it as before
+        torch.cuda.synchronize()
+        n_alloc, free0 = L.gbpcg_device_allocations(), torch.cuda.mem_get_info()[0]
+        rc, x, st = _noalloc(P, A, b, x0=x0, x0_zero=1, tol=TOL, max_iter=200000)
+        torch.cuda.synchronize()
+        if call == 1:
+            assert L.gbpcg_device_allocations() == n_alloc
+            assert torch.cuda.mem_get_info()[0] == free0
+        assert rc == 0, L.gbpcg_last_error()
         assert st.status == 0 and st.relres <= TOL
         assert _xerr(x_ref, x) <= XERR
         assert abs(st.iterations - st_ref["iterations"]) <= 2
+
+
+def test_noalloc_warm_start_matches_pcg_solve(P):
+    """A nonzero x0 (a partly converged iterate) gathered into the static
+    array: the same iterations and solution as pcg_solve from that x0."""
+    d = P.FemSystem(2, 1, 150, 1, 1, 7)
+    A = d.to_sell(32, 256)
+    b = d.lift(d.dirichlet(1))[:, 0].contiguous()
+    x_part, _ = A.solve(b, tol=1e-4, max_iter=200000)
+    x_ref, st_ref = A.solve(b, x0=x_part, tol=TOL, max_iter=200000)
+    rc, x, st = _noalloc(P, A, b, x0=x_part, tol=TOL, max_iter=200000)
+    assert rc == 0, P.gbpcg.lib().gbpcg_last_error()
+    assert st.status == 0 and st.relres <= TOL
+    assert abs(st.iterations - st_ref["iterations"]) <= 2
+    assert _xerr(x_ref, x) <= XERR
 
 
 def test_noalloc_second_system_after_first(P):
