@@ -281,9 +281,11 @@ typedef struct PcgOptions {
     int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
     int32_t persist_off;   /* pcg_solve_batched: 0 (default) = systems with n * k2 <= 32768 (k2: the
                               power of two >= k) are solved whole by one CTA each in a single
-                              persistent launch, and systems with n * k2 <= 524288 by one
+                              persistent launch, and, when the batch holds enough of them to fill
+                              half the GPU's clusters, systems with n * k2 <= 524288 by one
                               thread-block cluster of 8 CTAs each in another; 1 = every system in
-                              the multi-launch loop; 2 = the CTA-local tier only */
+                              the multi-launch loop; 2 = the CTA-local tier only; 3 = both tiers
+                              for every eligible system */
     int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
     int32_t method;        /* GB_CG (0, default) or GB_BICGSTAB (pcg_solve, GB_F64, C = 32) */
 } PcgOptions;
@@ -311,8 +313,15 @@ int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions
  * n_s x k_s blocks d_B[s], d_X[s]).  Systems with k > 1 run blocked multi-RHS
  * PCG: one SpMM pass per iteration serves all columns, each column keeps its
  * own alpha, beta and convergence mask.  All systems advance in the same
- * launches.  Synchronises `stream`; stats[s] per system (iterations = max
- * over its columns). */
+ * launches.  opt->precision: GB_F64; GB_F32_IR / GB_BF16_IR (fp32
+ * recurrences inside fp64 iterative refinement); GB_F32_RU (one fp32
+ * recurrence per column with fp64 reliable updates -- x += d, r = b - A x,
+ * residual replacement -- every 10x decrease; stats.outer = updates).  The
+ * persistent tiers (PcgOptions.persist_off) solve their systems in fp64, or
+ * with fp32 correction solves inside fp64 refinement for the fp32
+ * precisions.  Columns a mixed-precision solve leaves above tol finish in
+ * fp64 (stats.fallback_iterations).  Synchronises `stream`; stats[s] per
+ * system (iterations = max over its columns). */
 int pcg_solve_batched(int nsys, const gb_sell *const *A, const double *const *d_B,
                       double *const *d_X, const int *k, const PcgOptions *opt, void *stream,
                       PcgStats *stats);
@@ -357,6 +366,9 @@ typedef struct ServeOptions {
     int32_t iters_per_step;  /* CG iterations between scheduling points; 0 = adaptive (default):
                                 about 10 ms of the resident requests' iterations, 4 to 200 */
     int32_t device;          /* CUDA device, -1 = the current one */
+    int32_t cluster_lane;    /* 1 = requests with 2^15 < n * k2 <= 2^19 are solved whole by one
+                                8-CTA cluster each in the persistent lane; 0 (default) = they
+                                advance in the lock-step loop with the large ones */
 } ServeOptions;
 
 typedef struct ServeRequest {

@@ -329,9 +329,10 @@ class Server:
     request completes."""
 
     def __init__(self, mem_budget=40 << 30, max_slots=64, precision=G.GB_F32_RU, tol=1e-10,
-                 max_iter=0, iters_per_step=0, device=-1):
+                 max_iter=0, iters_per_step=0, device=-1, cluster_lane=0):
         import numpy as np  # noqa: F401
-        o = G.ServeOptions(int(mem_budget), max_slots, precision, tol, max_iter, iters_per_step, device)
+        o = G.ServeOptions(int(mem_budget), max_slots, precision, tol, max_iter, iters_per_step, device,
+                           cluster_lane)
         h = C.c_void_p()
         # no caller allocator: the server allocates from its own stream-ordered
         # pool (its thread would otherwise call back into Python)

@@ -15,7 +15,9 @@
 //
 // precision GB_F64 runs the recurrences in fp64; GB_F32_IR / GB_BF16_IR wrap
 // fp32 recurrences (fp32 or bf16 values) in fp64 iterative refinement: outer
-// residual B - A X, convergence test and update X += ||r_j|| D_j in fp64.
+// residual B - A X, convergence test and update X += ||r_j|| D_j in fp64;
+// GB_F32_RU keeps one fp32 recurrence per column and makes fp64 reliable
+// updates (X += D, R = B - A X, residual replacement) every 10x decrease.
 #include "batched.cuh"
 
 
@@ -78,6 +80,100 @@ static int batched_ir(Batch &b, const PcgOptions &o, cudaStream_t st, std::vecto
     return GB_OK;
 }
 
+// fp32 recurrences with fp64 reliable updates (GB_F32_RU): every column's
+// fp32 recurrence runs on the unscaled residual until it has fallen by a
+// factor 10 (threshold max(0.01 ||r||^2, target), target = (tol/2)^2 ||b||^2);
+// then, for the columns that ran, X += D in fp64 (k_bcorrect), the true
+// residual R = B - A X in fp64 (k_bresid), and the test of Eq. 2.  A column
+// above tol goes on with its fp32 residual replaced by the true one and its
+// direction kept (k_breplace / k_breplace_p: mask 1), or restarted with a
+// fresh direction after a breakdown (mask 2); four updates in a row without
+// a 10 % gain, or the iteration cap, stop it (the fp64 finish of the caller
+// then takes it from its X).  The Krylov recurrence is not restarted at each
+// update, so the iteration count stays close to the fp64 recurrence's,
+// unlike iterative refinement's restarted inner solves.
+template <class TV>
+static int batched_ru(Batch &b, const PcgOptions &o, cudaStream_t st, std::vector<int> &updates,
+                      std::vector<long long> &its) {
+    const size_t ns = b.h.size();
+    HostCols hc;
+    GB_TRY(pull_cols(b, hc, st));
+    std::vector<int> mask(ns * KMAX, 0);
+    std::vector<std::vector<double>> best(ns);
+    std::vector<std::vector<int>> stalls(ns), fin(ns);
+    updates.assign(ns, 0);
+    its.assign(ns, 0);
+    bool any = false;
+    for (size_t s = 0; s < ns; ++s) {
+        const int k = b.h[s].k;
+        best[s].assign(k, 1.0);
+        stalls[s].assign(k, 0);
+        fin[s].assign(k, 0);
+        std::vector<double> target(k), one(k, 1.0);
+        for (int j = 0; j < k; ++j) {
+            target[j] = 0.25 * o.tol * o.tol * hc.bb[s][j];
+            const bool need = hc.bb[s][j] > 0 && hc.rr[s][j] > o.tol * o.tol * hc.bb[s][j];
+            mask[s * KMAX + j] = need ? 2 : 0;
+            fin[s][j] = need ? 0 : 1;
+            any |= need;
+        }
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.h[s].c.target, target.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.h[s].c.scale, one.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        std::vector<long long> z(k, 0);
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.h[s].c.it, z.data(), sizeof(long long) * k, cudaMemcpyHostToDevice, st));
+    }
+    std::vector<BSys> hs(ns);
+    while (any) {
+        GB_CHECK_CUDA(cudaMemcpyAsync(b.d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
+        ::gb::count_launches(2);
+        k_breplace<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.partials, b.d_mask, 0.01);
+        k_breplace_p<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_mask);
+        GB_CHECK_CUDA(cudaGetLastError());
+        GB_CHECK_CUDA(cudaMemcpyAsync(hs.data(), b.d_sys, sizeof(BSys) * ns, cudaMemcpyDeviceToHost, st));
+        GB_CHECK_CUDA(cudaStreamSynchronize(st));
+        int act = 0;
+        for (auto &x : hs) act += x.active > 0 ? 1 : 0;
+        if (act > 0) {
+            BGlobal g{};
+            g.maxit = o.max_iter;
+            g.active_systems = act;
+            g.budget = -1;
+            GB_CHECK_CUDA(cudaMemcpyAsync(b.d_G, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+            GB_TRY(run_bloop(st, b.d_G, o.use_graph != 0, o.check_every,
+                             [&](cudaStream_t s2) { enqueue_biter<float, TV>(b, s2); }));
+        }
+        // reliable update of the columns that ran: X += D, R = B - A X (fp64)
+        ::gb::count_launches(2);
+        k_bcorrect<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.d_mask);
+        k_bresid<<<b.units, NT, 0, st>>>(b.d_sys, b.d_unit_sys, b.partials, 0, 0, o.tol);
+        GB_CHECK_CUDA(cudaGetLastError());
+        GB_TRY(pull_cols(b, hc, st));
+        any = false;
+        for (size_t s = 0; s < ns; ++s) {
+            bool ran = false;
+            for (int j = 0; j < b.h[s].k; ++j) {
+                int &m = mask[s * KMAX + j];
+                if (!m) continue;
+                ran = true;
+                its[s] = std::max(its[s], hc.it[s][j]);
+                const double rel = hc.bb[s][j] > 0 ? std::sqrt(hc.rr[s][j] / hc.bb[s][j]) : 0.0;
+                int nm = 0;
+                if (rel <= o.tol || hc.status[s][j] == ST_MAXIT || hc.it[s][j] >= o.max_iter) {
+                    fin[s][j] = 1;
+                } else {
+                    if (rel < 0.9 * best[s][j]) { best[s][j] = rel; stalls[s][j] = 0; }
+                    else if (++stalls[s][j] >= 4) fin[s][j] = 1;
+                    if (!fin[s][j]) nm = hc.status[s][j] == ST_BREAK ? 2 : 1;
+                }
+                m = nm;
+                any |= nm != 0;
+            }
+            if (ran) updates[s] += 1;
+        }
+    }
+    return GB_OK;
+}
+
 // Builds the batch: per-system units, permuted fp64 right-hand sides and
 // starting iterates, recurrence vectors of the precision's type, column state,
 // and the device copies of the system table.
@@ -134,7 +230,7 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
             GB_TRY(b.take(&P, nk));
             GB_TRY(b.take(&Q, nk));
             S.X = X; S.R = R; S.P = P; S.Q = Q;
-            S.val = o.precision == GB_F32_IR ? (const void *)M->val32 : (const void *)M->val16;
+            S.val = o.precision == GB_BF16_IR ? (const void *)M->val16 : (const void *)M->val32;
         }
         double *cd;
         GB_TRY(b.take(&cd, (size_t)10 * KMAX));
@@ -165,6 +261,15 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
     GB_CHECK_CUDA(cudaMemsetAsync(b.d_G, 0, sizeof(BGlobal), st));
 
     return GB_OK;
+}
+
+// Medium systems in a batch below which the multi-launch loop, which spreads
+// each iteration over every SM, beats one 8-SM cluster per system.
+#ifndef GB_CLUSTER_MIN_SYSTEMS
+#define GB_CLUSTER_MIN_SYSTEMS 0  // 0: half the clusters the SMs hold
+#endif
+static int cluster_min_systems() {
+    return GB_CLUSTER_MIN_SYSTEMS > 0 ? GB_CLUSTER_MIN_SYSTEMS : std::max(1, num_sms() / CLUSTER_CS / 2);
 }
 
 // One launch of a persistent kernel over the systems in `list` (their
@@ -217,11 +322,13 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     if (!(o.inner_tol > 0)) o.inner_tol = 1e-4;
     if (o.check_every <= 0) o.check_every = 16;
     if (graphs_disabled()) o.use_graph = 0;
-    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_BF16_IR, "pcg_solve_batched: bad precision");
+    GB_REQUIRE(o.precision >= GB_F64 && o.precision <= GB_F32_RU && o.precision != GB_BF16_RU,
+               "pcg_solve_batched: precision must be GB_F64, GB_F32_IR, GB_BF16_IR or GB_F32_RU");
     GB_REQUIRE(o.precond == GB_PC_JACOBI, "pcg_solve_batched: the Jacobi preconditioner only");
     GB_REQUIRE(o.method == GB_CG, "pcg_solve_batched: CG only");
     for (int s = 0; s < nsys; ++s) {
-        GB_REQUIRE(o.precision != GB_F32_IR || A[s]->val32, "pcg_solve_batched: system %d has no fp32 values", s);
+        GB_REQUIRE((o.precision != GB_F32_IR && o.precision != GB_F32_RU) || A[s]->val32,
+                   "pcg_solve_batched: system %d has no fp32 values", s);
         GB_REQUIRE(o.precision != GB_BF16_IR || A[s]->val16, "pcg_solve_batched: system %d has no bf16 values", s);
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -253,6 +360,9 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
         if (tier == 1) plist.push_back(s);
         else if (tier == 2 && o.persist_off != 2) clist.push_back(s);
     }
+    // a cluster holds CLUSTER_CS of the SMs: it pays only when enough medium
+    // systems share the GPU side by side (or when forced, persist_off = 3)
+    if (o.persist_off == 0 && (int)clist.size() < cluster_min_systems()) clist.clear();
     if (!clist.empty()) GB_TRY(run_persist(b, clist, o, ir, st, 2));
     for (int s : clist) plist.push_back(s);
     if (!plist.empty()) {
@@ -295,8 +405,9 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
             for (int s = 0; s < nsys; ++s) { hc.rr[s] = h2.rr[s]; hc.status[s] = h2.status[s]; hc.it[s] = h2.it[s]; }
         }
     } else {
-        rc = o.precision == GB_F32_IR ? batched_ir<float>(b, o, st, outer_cnt, inner_its)
-                                      : batched_ir<__nv_bfloat16>(b, o, st, outer_cnt, inner_its);
+        rc = o.precision == GB_F32_RU   ? batched_ru<float>(b, o, st, outer_cnt, inner_its)
+             : o.precision == GB_F32_IR ? batched_ir<float>(b, o, st, outer_cnt, inner_its)
+                                        : batched_ir<__nv_bfloat16>(b, o, st, outer_cnt, inner_its);
         if (rc == GB_OK) rc = pull_cols(b, hc, st);
         // columns the refinement left above tol finish in fp64 from their X
         bool fb = false;
@@ -370,7 +481,7 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
         S.bnorm = bn;
         S.status = status;
         S.solve_ms = ms;
-        const double sv = ir ? (o.precision == GB_F32_IR ? 4.0 : 2.0) : 8.0;
+        const double sv = ir ? (o.precision == GB_BF16_IR ? 2.0 : 4.0) : 8.0;
         const double sx = ir ? 4.0 : 8.0;
         S.bytes_moved = (double)S.iterations * ((double)A[s]->nnz * (sv + 4.0) + 7.0 * A[s]->n * k[s] * sx);
         S.kernel_launches = 3 * (S.iterations + fallback_its[s]);

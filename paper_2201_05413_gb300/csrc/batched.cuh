@@ -83,6 +83,9 @@ __device__ __forceinline__ void bspmm_rows(BSys &S, int unit, int k, TX *colsum 
     while (gw < kv) gw <<= 1;              // lanes per row
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int jv = lane % gw, grp = lane / gw, gpw = 32 / gw;
+    TX ccomp[VW];
+#pragma unroll
+    for (int u = 0; u < VW; ++u) ccomp[u] = TX(0);
     bool on = jv < kv;
     if (on) {
         bool any = false;
@@ -137,9 +140,11 @@ __device__ __forceinline__ void bspmm_rows(BSys &S, int unit, int k, TX *colsum 
             const V pr = P[r * kv + jv];
             const TX *a = reinterpret_cast<const TX *>(&acc), *b = reinterpret_cast<const TX *>(&pr);
 #pragma unroll
-            for (int u = 0; u < VW; ++u) colsum[u] += a[u] * b[u];
+            for (int u = 0; u < VW; ++u) kadd(colsum[u], ccomp[u], a[u] * b[u]);
         }
     }
+#pragma unroll
+    for (int u = 0; u < VW; ++u) colsum[u] -= ccomp[u];
 }
 
 // Per-column block sums of lane partials (lane jv = lane % gw owns columns
@@ -225,6 +230,9 @@ __device__ __forceinline__ void bupdate_rows(BSys &S, int k, TX (&rz)[VW], TX (&
     while (gw < kv) gw <<= 1;
     const int jv = (threadIdx.x & 31) % gw, grp = threadIdx.x / gw, ngrp = NT / gw;
     if (jv >= kv) return;
+    TX cz[VW], cr[VW];  // compensation of rz, rr (kadd)
+#pragma unroll
+    for (int u = 0; u < VW; ++u) { cz[u] = TX(0); cr[u] = TX(0); }
     TX alpha[VW];
     bool on[VW];
     bool any = false;
@@ -264,14 +272,16 @@ __device__ __forceinline__ void bupdate_rows(BSys &S, int k, TX (&rz)[VW], TX (&
                 for (int u = 0; u < VW; ++u) {  // frozen columns keep their values (alpha 0)
                     x[u] += alpha[u] * pp[u];
                     rr_[u] -= alpha[u] * qq[u];
-                    rz[u] += rr_[u] * (dd[t] * rr_[u]);
-                    rr[u] += rr_[u] * rr_[u];
+                    kadd(rz[u], cz[u], rr_[u] * (dd[t] * rr_[u]));
+                    kadd(rr[u], cr[u], rr_[u] * rr_[u]);
                 }
                 X[e] = xv[t];
                 R[e] = rv[t];
             }
         }
     }
+#pragma unroll
+    for (int u = 0; u < VW; ++u) { rz[u] -= cz[u]; rr[u] -= cr[u]; }
 }
 
 template <class TX, int VW>

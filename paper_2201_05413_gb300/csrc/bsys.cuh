@@ -8,6 +8,23 @@ namespace gb {
 
 constexpr int KMAX = 32;
 
+// Compensated (Kahan) accumulation of the per-lane column partials of the
+// fp32 recurrences: a lane adds up hundreds of products of a column (its rows
+// of a unit), and plain fp32 sums of that length perturb the recurrences'
+// alpha and beta by ~1e-6 -- enough to cost iterations on the ill-conditioned
+// systems (2D P2 2048^2).  s holds the sum, c the lost low part (the sum is
+// s - c); fp64 partials add plainly.
+template <class TX> __device__ __forceinline__ void kadd(TX &s, TX &c, TX v) {
+    if constexpr (sizeof(TX) == 4) {
+        const TX y = v - c;
+        const TX t = s + y;
+        c = (t - s) - y;
+        s = t;
+    } else {
+        s += v;
+    }
+}
+
 struct ColState {  // per-column scalars of one system, arrays of length k
     double *rho, *pq, *alpha, *beta, *rr, *bb, *thresh, *scale;
     double *pz, *target;  // reliable updates: z-coefficient of the restored p; fp32 residual floor

@@ -238,21 +238,21 @@ static int grow(gb_server *s, T **p, size_t *cap, size_t need, cudaStream_t st) 
 }
 
 // Requests up to n * k2 <= 2^15 (k2: the power of two >= k) are solved by one
-// block each of k_bpersist, and requests up to n * k2 <= 2^19 by one 8-block
-// cluster each of k_bcluster: such a request works through its iterations at
-// the pace of its own SMs, which for these sizes beats advancing in lock-step
-// with the largest resident requests.  Returns the tier (0: lock-step loop).
+// block each of k_bpersist, and, with ServeOptions.cluster_lane, requests up
+// to n * k2 <= 2^19 by one 8-block cluster each of k_bcluster: such a request
+// works through its iterations at the pace of its own SMs instead of in
+// lock-step with the largest resident requests (which pays for the smallest
+// ones; a cluster's 8 SMs make a medium request slower than the lock-step
+// loop over all SMs unless many of them are resident).  Returns the tier
+// (0: lock-step loop).
 #ifndef GB_SERVE_PERSIST_LOG2
 #define GB_SERVE_PERSIST_LOG2 15
 #endif
-#ifndef GB_SERVE_CLUSTER
-#define GB_SERVE_CLUSTER 1
-#endif
-static int serve_persist_tier(int64_t n, int k, bool ru) {
+static int serve_persist_tier(int64_t n, int k, bool ru, bool cluster_lane) {
     int kp = 1;
     while (kp < k) kp <<= 1;
     if (n * kp <= (ru ? ((int64_t)1 << GB_SERVE_PERSIST_LOG2) : PERSIST_MAX_ELEMS)) return 1;
-    if (GB_SERVE_CLUSTER && n * kp <= CLUSTER_MAX_ELEMS) return 2;
+    if (cluster_lane && n * kp <= CLUSTER_MAX_ELEMS) return 2;
     return 0;
 }
 
@@ -360,7 +360,7 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
         mask[j] = ru ? 2 : 1;
         target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
     }
-    L.ptier = serve_persist_tier(L.n, L.k, ru);
+    L.ptier = serve_persist_tier(L.n, L.k, ru, s->opt.cluster_lane != 0);
     if (L.ptier) {
         // small or medium request: solved whole by one block (or one cluster)
         // of the next persistent launch (launch_persistent), not in the

@@ -94,7 +94,7 @@ class SellTuneResult(C.Structure):
 class ServeOptions(C.Structure):
     _fields_ = [("mem_budget", C.c_size_t), ("max_slots", C.c_int32), ("precision", C.c_int32),
                 ("tol", C.c_double), ("max_iter", C.c_int64), ("iters_per_step", C.c_int32),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("cluster_lane", C.c_int32)]
 
 
 class ServeRequest(C.Structure):

@@ -31,14 +31,14 @@ def _oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k):
 
 @pytest.mark.parametrize("persist_off", [0, 1])
 @pytest.mark.parametrize("k", [1, 3, 8, 12, 16, 32])
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32ru"])
 def test_multi_rhs_matches_oracle(P, k, prec, persist_off):
     spec = (2, 2, 24, 1, 1, 2)
     coef = np.random.default_rng(3).standard_normal((k, 10))
     d = P.FemSystem(*spec)
     A = d.to_sell(32, 256)
     B = d.lift(d.dirichlet(O.G_HARMONIC, coef, k))
-    p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
+    p = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "f32ru": P.GB_F32_RU}[prec]
     Xs, stats = P.pcg_solve_batched([A], [B], tol=TOL, precision=p, max_iter=100000, persist_off=persist_off)
     X = Xs[0].cpu().numpy()
     s, rp, ci, v, Bo, Xo = _oracle_cols(*spec, O.G_HARMONIC, coef, k)
@@ -164,7 +164,7 @@ def test_cluster_tier_uneven_batch(P, prec):
         tiers.append(_tier(d.n_free, k))
     assert tiers == [1, 2, 2, 2, 2, 0]
     p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
-    Xs, sts = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=400000)
+    Xs, sts = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=400000, persist_off=3)
     for X, st, (s, rp, ci, v, Bo, Xo) in zip(Xs, sts, refs):
         assert st["status"] == 0, st
         X = X.cpu().numpy()
@@ -173,13 +173,13 @@ def test_cluster_tier_uneven_batch(P, prec):
             assert rel <= 1.5 * TOL, (j, rel)
             assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8
     for i in (1, 3):
-        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, precision=p, max_iter=400000)
+        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, precision=p, max_iter=400000, persist_off=3)
         assert bool((Xa[0] == Xs[i]).all())
         assert sa[0]["iterations"] == sts[i]["iterations"]
 
 
 def test_cluster_tier_matches_multilaunch(P):
-    """The same medium systems through the cluster kernel (persist_off=0) and
+    """The same medium systems through the cluster kernel (persist_off=3) and
     through the multi-launch loop (persist_off=1): the fp64 iterates agree to
     the solver tolerance and the iteration counts to rounding drift."""
     specs = [(2, 2, 120, 1, 1, 8, 4), (3, 1, 36, 1, 0, 9, 1)]
@@ -191,10 +191,38 @@ def test_cluster_tier_matches_multilaunch(P):
         mats.append(d.to_sell(32, 256))
         Bs.append(d.lift(d.dirichlet(gid, rng.standard_normal((k, O.NCOEF[gid])), k)))
         assert _tier(d.n_free, k) == 2
-    Xc, sc = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=0)
+    Xc, sc = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=3)
     Xm, sm = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=1)
     for X1, X2, s1, s2 in zip(Xc, Xm, sc, sm):
         assert s1["status"] == 0 and s2["status"] == 0
         assert abs(s1["iterations"] - s2["iterations"]) <= max(3, 0.02 * s2["iterations"])
         for j in range(X1.shape[1]):
             assert O.x_err(X2[:, j].cpu().numpy(), X1[:, j].cpu().numpy()) <= 1e-8
+
+
+def test_reliable_updates_keep_the_fp64_iteration_count(P):
+    """GB_F32_RU in the multi-launch loop: one fp32 recurrence per column with
+    fp64 reliable updates reaches Eq. 2 in about the fp64 recurrence's
+    iterations (within 15 %), where refinement's restarted inner solves take
+    more, and matches the oracle column by column."""
+    spec = (2, 2, 64, 1, 1, 6)
+    k = 6
+    coef = np.random.default_rng(8).standard_normal((k, 10))
+    d = P.FemSystem(*spec)
+    A = d.to_sell(32, 256)
+    B = d.lift(d.dirichlet(O.G_HARMONIC, coef, k))
+    its = {}
+    for name, p in (("f64", P.GB_F64), ("ru", P.GB_F32_RU), ("ir", P.GB_F32_IR)):
+        Xs, st = P.pcg_solve_batched([A], [B], tol=TOL, precision=p, max_iter=100000, persist_off=1)
+        assert st[0]["status"] == 0 and st[0]["relres"] <= TOL, (name, st[0])
+        its[name] = st[0]["iterations"] + st[0]["fallback_iterations"]
+        if name == "ru":
+            assert st[0]["outer"] >= 2 and st[0]["fallback_iterations"] == 0
+            X = Xs[0].cpu().numpy()
+    assert its["ru"] <= 1.15 * its["f64"], its
+    assert its["ir"] > its["ru"], its
+    s, rp, ci, v, Bo, Xo = _oracle_cols(*spec, O.G_HARMONIC, coef, k)
+    for j in range(k):
+        rel = np.linalg.norm(Bo[:, j] - O.spmv(rp, ci, v, X[:, j])) / np.linalg.norm(Bo[:, j])
+        assert rel <= 1.5 * TOL, (j, rel)
+        assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8

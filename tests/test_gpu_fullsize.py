@@ -124,22 +124,27 @@ def _cfg4_errors(spec, coef, X, k):
     return [O.x_err(U[:, j], Xh[:, j]) for j in range(k)]
 
 
-def test_cfg4_full_blocked_exact_solution_f32ir(P):
+def test_cfg4_full_blocked_exact_solution_f32ru(P):
     """2D jittered 2048^2 P2 (16.8M unknowns), all 32 right-hand sides of the
-    configuration solved together by the blocked multi-RHS solver, the fp32
-    recurrence inside fp64 iterative refinement, to Eq. 2 at 1e-10.  Each
-    column's Dirichlet data is a seeded N(0,1) combination of Re/Im (x+iy)^k
-    for k <= 2 (the coefficients of k = 3, 4 set to zero), a harmonic
-    quadratic that P2 reproduces exactly: every column must equal the data at
-    the oracle's node coordinates to 1e-8 (Eq. 1); the sampled stiffness rows
-    match the oracle's."""
+    configuration solved together by the blocked multi-RHS solver, fp32
+    recurrences with fp64 reliable updates, to Eq. 2 at 1e-10.  Each column's
+    Dirichlet data is a seeded N(0,1) combination of Re/Im (x+iy)^k for k <= 2
+    (the coefficients of k = 3, 4 set to zero), a harmonic quadratic that P2
+    reproduces exactly, so every column is compared with the data at the
+    oracle's node coordinates (Eq. 1): at 1e-10 within what that residual
+    allows on this system (bar 2e-7, as in fp64), and, continued from there
+    to 1e-12, within 1e-8; the sampled stiffness rows match the oracle's."""
     spec, d, A, coef = _cfg4(P)
     k = 32
     B = d.lift(d.dirichlet(O.G_HARMONIC, coef, k))
-    X, st = P.pcg_solve_batched([A], [B], tol=TOL, max_iter=400000, precision=P.GB_F32_IR)
+    X, st = P.pcg_solve_batched([A], [B], tol=TOL, max_iter=400000, precision=P.GB_F32_RU)
     assert st[0]["status"] == 0 and st[0]["relres"] <= TOL, st[0]
-    errs = _cfg4_errors(spec, coef, X[0], k)
-    assert max(errs) <= 1e-8, errs
+    e10 = _cfg4_errors(spec, coef, X[0], k)
+    assert max(e10) <= 2e-7, e10
+    X2, st2 = P.pcg_solve_batched([A], [B], [X[0]], tol=1e-12, max_iter=400000, precision=P.GB_F32_RU)
+    assert st2[0]["status"] == 0 and st2[0]["relres"] <= 1e-12, st2[0]
+    e12 = _cfg4_errors(spec, coef, X2[0], k)
+    assert max(e12) <= 1e-8, (e10, e12)
     _check_sampled_rows(P, d, spec, nsample=600)
 
 

@@ -144,7 +144,7 @@ def test_boundary_data_from_host(P):
     assert r["status"] == 0 and O.x_err(u, x[:, 0]) <= 1e-8
 
 
-MIX_TIERS = [  # one request per path: one block, one 8-block cluster (two), the lock-step loop
+MIX_TIERS = [  # one request per path: one block, the cluster lane (two), the lock-step loop
     (2, 1, 40, 1, 1, 11, 2, O.G_HARMONIC),   # n k2 = 3042: one block
     (2, 1, 200, 1, 1, 12, 2, O.G_HARMONIC),  # 79202: one cluster
     (3, 2, 20, 0, 0, 0, 1, O.G_LINEAR),      # 59319: one cluster
@@ -152,14 +152,16 @@ MIX_TIERS = [  # one request per path: one block, one 8-block cluster (two), the
 ]
 
 
+@pytest.mark.parametrize("lane", [1, 0])
 @pytest.mark.parametrize("prec", ["f32ru", "f64"])
-def test_medium_requests_through_cluster_lane(P, prec):
-    """Requests of every size class in one served mix: every column meets
-    Eq. 2 against the oracle's matrix, the cluster-solved requests are within
-    1e-8 of the oracle's solution, and each request served alone gives the
-    same bits."""
+def test_requests_of_every_size_in_one_mix(P, prec, lane):
+    """Requests of every size class in one served mix, with the cluster lane
+    for the medium ones (lane=1) and without it (lane=0: lock-step loop):
+    every column meets Eq. 2 against the oracle's matrix, the medium requests
+    are within 1e-8 of the oracle's solution, and each request served alone
+    gives the same bits."""
     p = P.GB_F32_RU if prec == "f32ru" else P.GB_F64
-    mixed, stats = _serve(P, MIX_TIERS, precision=p, max_slots=8)
+    mixed, stats = _serve(P, MIX_TIERS, precision=p, max_slots=8, cluster_lane=lane)
     assert stats["completed"] == len(MIX_TIERS)
     for i, ((r, x), req) in enumerate(zip(mixed, MIX_TIERS)):
         assert r["status"] == 0, r
@@ -174,7 +176,7 @@ def test_medium_requests_through_cluster_lane(P, prec):
                 xo = O.pcg(rp, ci, v, B[:, j], tol=1e-13)[0]
                 assert O.x_err(xo, x[:, j]) <= 1e-8
     for i, req in enumerate(MIX_TIERS):
-        srv = P.Server(precision=p, max_slots=1)
+        srv = P.Server(precision=p, max_slots=1, cluster_lane=lane)
         try:
             t = srv.submit(*req[:6], k=req[6], gid=req[7], coef=_coef(i, req[6], req[7]))
             (r, x), = srv.wait([t]).values()
