@@ -281,11 +281,9 @@ typedef struct PcgOptions {
     int32_t spmv_variant;  /* 0 = auto (TMA-staged slices for C = 32), 1 = one-row-per-lane loads */
     int32_t persist_off;   /* pcg_solve_batched: 0 (default) = systems with n * k2 <= 32768 (k2: the
                               power of two >= k) are solved whole by one CTA each in a single
-                              persistent launch, and, when the batch holds enough of them to fill
-                              half the GPU's clusters, systems with n * k2 <= 524288 by one
+                              persistent launch, and systems with n * k2 <= 65536 by one
                               thread-block cluster of 8 CTAs each in another; 1 = every system in
-                              the multi-launch loop; 2 = the CTA-local tier only; 3 = both tiers
-                              for every eligible system */
+                              the multi-launch loop; 2 = the CTA-local tier only */
     int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
     int32_t method;        /* GB_CG (0, default) or GB_BICGSTAB (pcg_solve, GB_F64, C = 32) */
 } PcgOptions;
@@ -366,7 +364,7 @@ typedef struct ServeOptions {
     int32_t iters_per_step;  /* CG iterations between scheduling points; 0 = adaptive (default):
                                 about 10 ms of the resident requests' iterations, 4 to 200 */
     int32_t device;          /* CUDA device, -1 = the current one */
-    int32_t cluster_lane;    /* 1 = requests with 2^15 < n * k2 <= 2^19 are solved whole by one
+    int32_t cluster_lane;    /* 1 = requests with 2^15 < n * k2 <= 2^16 are solved whole by one
                                 8-CTA cluster each in the persistent lane; 0 (default) = they
                                 advance in the lock-step loop with the large ones */
 } ServeOptions;

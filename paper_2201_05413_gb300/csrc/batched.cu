@@ -30,8 +30,7 @@ static int batched_ir(Batch &b, const PcgOptions &o, cudaStream_t st, std::vecto
     HostCols hc;
     std::vector<int> mask(ns * KMAX, 0);
     std::vector<double> prev;
-    outer_cnt.assign(ns, 0);
-    inner_its.assign(ns, 0);
+    // (outer_cnt / inner_its: zero on entry, or the persistent tiers' counts)
     // scale = ||r_j|| kept in c.scale; the fp32 recurrence works on R/||r||
     for (int outer = 0; outer < o.max_outer; ++outer) {
         GB_TRY(pull_cols(b, hc, st));
@@ -101,9 +100,7 @@ static int batched_ru(Batch &b, const PcgOptions &o, cudaStream_t st, std::vecto
     std::vector<int> mask(ns * KMAX, 0);
     std::vector<std::vector<double>> best(ns);
     std::vector<std::vector<int>> stalls(ns), fin(ns);
-    updates.assign(ns, 0);
-    its.assign(ns, 0);
-    bool any = false;
+    bool any = false;  // (updates / its: zero on entry, or the persistent tiers' counts)
     for (size_t s = 0; s < ns; ++s) {
         const int k = b.h[s].k;
         best[s].assign(k, 1.0);
@@ -263,15 +260,6 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
     return GB_OK;
 }
 
-// Medium systems in a batch below which the multi-launch loop, which spreads
-// each iteration over every SM, beats one 8-SM cluster per system.
-#ifndef GB_CLUSTER_MIN_SYSTEMS
-#define GB_CLUSTER_MIN_SYSTEMS 0  // 0: half the clusters the SMs hold
-#endif
-static int cluster_min_systems() {
-    return GB_CLUSTER_MIN_SYSTEMS > 0 ? GB_CLUSTER_MIN_SYSTEMS : std::max(1, num_sms() / CLUSTER_CS / 2);
-}
-
 // One launch of a persistent kernel over the systems in `list` (their
 // initial residuals already formed): fp64 CG for fp64 batches, fp32 correction
 // solves in fp64 refinement otherwise.  tier 1: one block per system
@@ -360,9 +348,6 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
         if (tier == 1) plist.push_back(s);
         else if (tier == 2 && o.persist_off != 2) clist.push_back(s);
     }
-    // a cluster holds CLUSTER_CS of the SMs: it pays only when enough medium
-    // systems share the GPU side by side (or when forced, persist_off = 3)
-    if (o.persist_off == 0 && (int)clist.size() < cluster_min_systems()) clist.clear();
     if (!clist.empty()) GB_TRY(run_persist(b, clist, o, ir, st, 2));
     for (int s : clist) plist.push_back(s);
     if (!plist.empty()) {

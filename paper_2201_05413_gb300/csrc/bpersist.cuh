@@ -27,7 +27,7 @@
 // system together:
 //   CtaGroup      one block (k_bpersist, small systems: n kp <= 2^15);
 //   ClusterGroup  the CS = 8 blocks of a thread-block cluster (k_bcluster,
-//                 medium systems: 2^15 < n kp <= 2^19).  Each block reduces
+//                 medium systems: 2^15 < n kp <= 2^16).  Each block reduces
 //                 its partial sums itself, publishes them in its shared
 //                 memory, and after a cluster barrier every block reads the 8
 //                 partials through distributed shared memory in rank order,
@@ -47,7 +47,12 @@ namespace gb {
 constexpr int PNT = 512;                         // threads per block
 constexpr int64_t PERSIST_MAX_ELEMS = 1 << 15;   // n * kp of a system the CTA-local kernel takes
 constexpr int CLUSTER_CS = 8;                    // blocks per cluster (the portable maximum)
-constexpr int64_t CLUSTER_MAX_ELEMS = 1 << 19;   // n * kp of a system the cluster kernel takes
+// n * kp of a system the cluster kernel takes: above 2^15 one block is too
+// slow, and above ~2^16 the multi-launch loop over every SM is faster than
+// 8 SMs per system even with 19 such systems side by side (2D P1 200^2: 47
+// against 53 ms alone, 97 against 90 ms for 19; 3D P1 48^3 with 2 columns: 51
+// against 14 ms alone, 134 against 61 ms for 19)
+constexpr int64_t CLUSTER_MAX_ELEMS = 1 << 16;
 
 struct PersistOpts {
     long long maxit;    // iterations per column (fp64) / inner iterations per outer step (fp32)

@@ -39,22 +39,6 @@ constexpr bool BSPMM_INTERLEAVE = GB_BSPMM_INTERLEAVE != 0;
 #ifndef GB_BSPMM_WIDE_GBUF
 #define GB_BSPMM_WIDE_GBUF 32
 #endif
-// Wide fp32 rows (G >= 4 lanes per row, P rows of 64 or 128 bytes) gather
-// their P slices with cp.async into a shared-memory ring of GB_BSPMM_NPS
-// column-steps per warp instead of registers: the copies in flight then cost
-// no registers, so a warp keeps NPS steps (NPS x 32 rows x K values) of
-// gathers in flight.  One block of 8 warps per SM (the ring's shared memory).
-#ifndef GB_BSPMM_CPA
-#define GB_BSPMM_CPA 1
-#endif
-#ifndef GB_BSPMM_NPS
-#define GB_BSPMM_NPS 5
-#endif
-template <class TX, int K> struct BspmmCpa {
-    static constexpr bool on = GB_BSPMM_CPA && sizeof(TX) == 4 && K * (int)sizeof(TX) >= 64;
-    static constexpr int NPS = GB_BSPMM_NPS;
-};
-
 template <class TX, int K> struct BspmmOcc {
     static constexpr int ACC = K * (int)sizeof(TX) / 4;  // accumulator registers
     // gather buffer: 16 registers; fp32 rows of 64 bytes or more (G >= 4
@@ -66,14 +50,8 @@ template <class TX, int K> struct BspmmOcc {
         (sizeof(TX) == 4 && K * (int)sizeof(TX) >= 64 && ACC + GB_BSPMM_WIDE_GBUF + 44 <= 128) ? GB_BSPMM_WIDE_GBUF
                                                                                               : 16;
     static constexpr int R = ACC + GBUF + 44;
-    static constexpr int blocks = BspmmCpa<TX, K>::on ? 1 : (R <= 64 ? 4 : (R <= 84 ? 3 : 2));
+    static constexpr int blocks = R <= 64 ? 4 : (R <= 84 ? 3 : 2);
 };
-
-__device__ __forceinline__ void cpa16(void *dst_smem, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // One warp's chunks c0, c0 + cs, ..., c0 + (nc - 1) cs of system S (cs = 1:
 // a contiguous range, streamed as one linear array; cs > 1: the chunks are
@@ -314,212 +292,7 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
     __syncwarp();
 }
 
-// The wide fp32 stream with cp.async-staged gathers (BspmmCpa).  The matrix
-// streams through the TMA ring as in bspmm_warp_stream; step t's P slices go
-// to slot t mod NPS of the warp's staging ring ps[NPS][G][32] (16 bytes per
-// lane and pass, laid out so a warp's accesses are contiguous), NPS steps
-// ahead of the step being accumulated.  Lane l copies exactly the slices it
-// later reads (rows q R + l / G, columns (l mod G) VW ..), so its own
-// cp.async.wait_group orders them; one commit group per step keeps the
-// groups retiring in step order.
-template <class TV, int K>
-__device__ __forceinline__ void bspmm_warp_stream_cpa(const BSys &S, int64_t c0, int64_t nc, int cs, Tma2Ring<TV> &sm,
-                                                      uint64_t *bars, uint4 (*ps)[BSlice<float, K>::G][32],
-                                                      bool *timed_out, float (&dot)[BSlice<float, K>::VW]) {
-    using TX = float;
-    constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
-    constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW, R = BSlice<TX, K>::R;
-    constexpr int NPS = BspmmCpa<TX, K>::NPS;
-    static_assert(VW * sizeof(TX) == 16, "one 16-byte slice per lane and pass");
-    static_assert(NPS >= 1 && NPS <= SJ, "the gathers run at most one TMA stage ahead");
-    constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane / G, slice = lane % G;
-    const int c0col = slice * VW;
-    const SellView &A = S.A;
-    const TV *__restrict__ val = (const TV *)S.val;
-    const TX *__restrict__ P = (const TX *)S.P;
-    TX *__restrict__ Q = (TX *)S.Q;
-#pragma unroll
-    for (int u = 0; u < VW; ++u) dot[u] = TX(0);
-    if (nc <= 0) return;
-    TX dcomp[VW];  // compensation of dot (kadd)
-#pragma unroll
-    for (int u = 0; u < VW; ++u) dcomp[u] = TX(0);
-    const int64_t e0 = __ldg(A.chunk_ptr + c0);
-    int64_t nsteps;
-    if (cs == 1) {
-        nsteps = (__ldg(A.chunk_ptr + c0 + nc) - e0) >> 5;
-    } else {
-        int64_t t = 0;
-        for (int64_t i = lane; i < nc; i += 32) t += __ldg(A.chunk_w + c0 + i * cs);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-        nsteps = t;
-    }
-    const int64_t nstages = (nsteps + SJ - 1) / SJ;
-    uint64_t pol = 0;
-    if (GB_TMA2_EVICT_FIRST && lane == 0) pol = l2_policy_evict_first();
-    int64_t issued = 0;
-    int64_t ic = 0, ioff = 0;
-    auto issue = [&](int64_t st) {
-        issued = st + 1;
-        if (lane == 0) {
-            const int b = (int)(st % NB);
-            const int sj = (int)min((int64_t)SJ, nsteps - st * SJ);
-            mbar_expect_tx(&bars[b], (uint32_t)(sj * 32 * (sizeof(int32_t) + sizeof(TV))));
-            if (cs == 1) {
-                const int64_t off = e0 + st * SJ * 32;
-                bulk_g2s_pol(sm.col[b], A.col + off, (uint32_t)(sj * 32 * sizeof(int32_t)), &bars[b], pol);
-                bulk_g2s_pol(sm.val[b], val + off, (uint32_t)(sj * 32 * sizeof(TV)), &bars[b], pol);
-            } else {
-                int filled = 0;
-                while (filled < sj && ic < nc) {
-                    const int64_t c = c0 + ic * cs;
-                    const int64_t w = __ldg(A.chunk_w + c);
-                    const int take = (int)min((int64_t)(sj - filled), w - ioff);
-                    if (take > 0) {
-                        const int64_t off = __ldg(A.chunk_ptr + c) + ioff * 32;
-                        bulk_g2s_pol(sm.col[b] + filled * 32, A.col + off, (uint32_t)(take * 32 * sizeof(int32_t)),
-                                     &bars[b], pol);
-                        bulk_g2s_pol(sm.val[b] + filled * 32, val + off, (uint32_t)(take * 32 * sizeof(TV)),
-                                     &bars[b], pol);
-                        filled += take;
-                        ioff += take;
-                    }
-                    if (ioff >= w) {
-                        ++ic;
-                        ioff = 0;
-                    }
-                }
-            }
-        }
-    };
-    for (int64_t st = 0; st < nstages && st < NB; ++st) issue(st);
-    int64_t waited = -1;  // the last stage whose copies this warp has seen land
-    auto wait_stage = [&](int64_t st) -> bool {
-        while (waited < st) {
-            ++waited;
-            const bool ok = mbar_wait(&bars[waited % NB], (uint32_t)((waited / NB) & 1));
-            if (!__all_sync(FULL, ok)) return false;
-        }
-        return true;
-    };
-    auto gather = [&](int64_t t) {  // step t's P slices into slot t mod NPS
-        const int32_t *cst = sm.col[(int)((t / SJ) % NB)] + (int)(t % SJ) * 32;
-        uint4(*dst)[32] = ps[(int)(t % NPS)];
-#pragma unroll
-        for (int q = 0; q < G; ++q) cpa16(&dst[q][lane], P + (int64_t)cst[q * R + sub] * K + c0col);
-    };
-    auto stq = [&](int64_t row, const TX (&v)[VW]) {
-        Pack<TX, VW> t;
-#pragma unroll
-        for (int u = 0; u < VW; ++u) t.v[u] = v[u];
-        *reinterpret_cast<Pack<TX, VW> *>(Q + row * K + c0col) = t;
-    };
-    int64_t tb = 0;
-    int ci = -1, left = 0;
-    int wv = (lane < nc) ? __ldg(A.chunk_w + c0 + (int64_t)lane * cs) : 0;
-    int64_t rbase = 0;
-    TX acc[G][VW];
-#pragma unroll
-    for (int q = 0; q < G; ++q)
-#pragma unroll
-        for (int u = 0; u < VW; ++u) acc[q][u] = TX(0);
-    auto next_chunk = [&]() {
-        do {
-            if (++ci == 32) {
-                tb += 32;
-                ci = 0;
-                wv = (tb + lane < nc) ? __ldg(A.chunk_w + c0 + (tb + lane) * cs) : 0;
-            }
-            left = __shfl_sync(FULL, wv, ci);
-            rbase = (c0 + (tb + ci) * cs) * 32;
-            if (left == 0 && tb + ci < nc) {  // an all-empty chunk: its rows of Q are zero
-                TX z[VW];
-#pragma unroll
-                for (int u = 0; u < VW; ++u) z[u] = TX(0);
-#pragma unroll
-                for (int q = 0; q < G; ++q)
-                    if (rbase + q * R + sub < A.n) stq(rbase + q * R + sub, z);
-            }
-        } while (left == 0 && tb + ci < nc);
-    };
-    next_chunk();
-    auto flush = [&]() {  // chunk complete (warp-uniform)
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const int64_t row = rbase + q * R + sub;
-            if (row < A.n) {
-                stq(row, acc[q]);
-                const Pack<TX, VW> pr = *reinterpret_cast<const Pack<TX, VW> *>(P + row * K + c0col);
-#pragma unroll
-                for (int u = 0; u < VW; ++u) kadd(dot[u], dcomp[u], pr.v[u] * acc[q][u]);
-            }
-#pragma unroll
-            for (int u = 0; u < VW; ++u) acc[q][u] = TX(0);
-        }
-        next_chunk();
-    };
-    bool failed = false;
-    if (nsteps > 0 && !wait_stage(0)) failed = true;
-    if (!failed && nsteps > 0)
-        for (int64_t t = 0; t < NPS; ++t) {
-            if (t < nsteps) gather(t);
-            cpa_commit();
-        }
-    for (int64_t j = 0; j < nsteps && !failed; ++j) {
-        cpa_wait<NPS - 1>();  // step j's slices have landed (groups retire in order)
-        const int64_t st = j / SJ;
-        const int pos = (int)(j % SJ);
-        const TV *vs = sm.val[(int)(st % NB)] + pos * 32;
-        const uint4(*src)[32] = ps[(int)(j % NPS)];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-            const uint4 w4 = src[q][lane];
-            const TX v = to_tx<TX>(vs[q * R + sub]);
-            acc[q][0] += v * __uint_as_float(w4.x);
-            acc[q][1] += v * __uint_as_float(w4.y);
-            acc[q][2] += v * __uint_as_float(w4.z);
-            acc[q][3] += v * __uint_as_float(w4.w);
-        }
-        if (--left == 0) flush();
-        const int64_t t = j + NPS;  // refill this slot (this lane read it above)
-        if (t < nsteps) {
-            if (!wait_stage(t / SJ)) { failed = true; break; }
-            gather(t);
-        }
-        cpa_commit();
-        if (pos == SJ - 1 || j == nsteps - 1) {  // stage st consumed: its buffer takes stage st + NB
-            __syncwarp();
-            fence_proxy_async();
-            if (st + NB < nstages) issue(st + NB);
-        }
-    }
-    cpa_wait<0>();
-    if (failed) {
-        *timed_out = true;
-        if (lane == 0)
-            for (int64_t s2 = waited + 1; s2 < issued; ++s2)
-                (void)mbar_wait(&bars[s2 % NB], (uint32_t)((s2 / NB) & 1));
-    }
-#pragma unroll
-    for (int u = 0; u < VW; ++u) dot[u] -= dcomp[u];
-    __syncwarp();
-}
-
-// dynamic shared memory of k_bspmm_tma<TX, TV, K>: the TMA ring and its
-// barriers, and for the cp.async variant the warps' P staging rings
-template <class TX, class TV, int K> struct BspmmPs {
-    static constexpr size_t offset = (tma2_smem_bytes<TV>() + 15) / 16 * 16;
-};
-template <class TX, class TV, int K> constexpr size_t bspmm_ps_offset() { return BspmmPs<TX, TV, K>::offset; }
-template <class TX, class TV, int K> constexpr size_t bspmm_tma_smem() {
-    return BspmmCpa<TX, K>::on ? bspmm_ps_offset<TX, TV, K>() + (size_t)TMA_WARPS * BspmmCpa<TX, K>::NPS *
-                                                                       BSlice<TX, K>::G * 32 * sizeof(uint4)
-                               : tma2_smem_bytes<TV>();
-}
-
+template <class TV> constexpr size_t bspmm_tma_smem() { return tma2_smem_bytes<TV>(); }
 
 template <class TX, class TV, int K>
 __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))
@@ -551,19 +324,7 @@ __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))
     bool timed_out = false;
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW;
     TX dot[VW];
-    bool staged = false;
-    if constexpr (BspmmCpa<TX, K>::on) {
-        if (S.k == K) {  // full width: 16-byte slices of P rows of stride K
-            staged = true;
-            constexpr int NPS = BspmmCpa<TX, K>::NPS;
-            uint4(*ps)[NPS][G][32] = reinterpret_cast<uint4(*)[NPS][G][32]>(smem_raw + BspmmPs<TX, TV, K>::offset);
-            const int64_t w0 = uc0 + warp;  // chunks interleaved across the warps, as below
-            const int64_t nc = w0 < uc1 ? (uc1 - w0 + TMA_WARPS - 1) / TMA_WARPS : 0;
-            bspmm_warp_stream_cpa<TV, K>(S, w0, nc, TMA_WARPS, bufs[warp], &bars[NB * warp], ps[warp], &timed_out,
-                                         dot);
-        }
-    }
-    if (!staged && BSPMM_INTERLEAVE && G > 1 && sizeof(TX) == 4) {
+    if (BSPMM_INTERLEAVE && G > 1 && sizeof(TX) == 4) {
         // fp32 rows of wide P blocks (G lanes per row): warp w takes chunks
         // uc0 + w, uc0 + w + 8, ..., so the block's 8 warps work on
         // neighbouring chunks (one sorting window of 256 rows at a time) and
@@ -573,7 +334,7 @@ __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))
         const int64_t w0 = uc0 + warp;
         const int64_t nc = w0 < uc1 ? (uc1 - w0 + TMA_WARPS - 1) / TMA_WARPS : 0;
         bspmm_warp_stream<TX, TV, K>(S, w0, nc, TMA_WARPS, bufs[warp], &bars[NB * warp], &timed_out, dot);
-    } else if (!staged) {
+    } else {
         const int64_t cpw = (cpu + TMA_WARPS - 1) / TMA_WARPS;
         const int64_t wc0 = min(uc1, uc0 + warp * cpw), wc1 = min(uc1, wc0 + cpw);
         bspmm_warp_stream<TX, TV, K>(S, wc0, wc1 - wc0, 1, bufs[warp], &bars[NB * warp], &timed_out, dot);
@@ -620,7 +381,7 @@ static void launch_bspmm_tma(int K, int unit_base, int units, BSys *d_sys, const
     if (units <= 0) return;
 #define GB_BSPMM_CASE(KK)                                                                                     \
     case KK: {                                                                                                \
-        constexpr int smem = (int)bspmm_tma_smem<TX, TV, KK>();                                               \
+        constexpr int smem = (int)bspmm_tma_smem<TV>();                                                      \
         static bool attr = false;                                                                             \
         if (!attr) {                                                                                          \
             cudaFuncSetAttribute(k_bspmm_tma<TX, TV, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \

@@ -239,7 +239,7 @@ static int grow(gb_server *s, T **p, size_t *cap, size_t need, cudaStream_t st) 
 
 // Requests up to n * k2 <= 2^15 (k2: the power of two >= k) are solved by one
 // block each of k_bpersist, and, with ServeOptions.cluster_lane, requests up
-// to n * k2 <= 2^19 by one 8-block cluster each of k_bcluster: such a request
+// to n * k2 <= 2^16 by one 8-block cluster each of k_bcluster: such a request
 // works through its iterations at the pace of its own SMs instead of in
 // lock-step with the largest resident requests (which pays for the smallest
 // ones; a cluster's 8 SMs make a medium request slower than the lock-step

@@ -139,19 +139,19 @@ def _tier(n, k):
     kp = 1
     while kp < k:
         kp *= 2
-    return 1 if n * kp <= 1 << 15 else (2 if n * kp <= 1 << 19 else 0)
+    return 1 if n * kp <= 1 << 15 else (2 if n * kp <= 1 << 16 else 0)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_cluster_tier_uneven_batch(P, prec):
-    """An uneven batch of serving-mix shapes spanning the three paths: a small
-    system (one CTA), medium ones (one 8-CTA cluster each: 2D P1 300^2, 2D P2
-    150^2 with 3 columns, 3D P1 40^3 with 2, 3D P2 24^3) and a large one (the
-    multi-launch loop).  Every column meets Eq. 2 against the oracle's matrix
-    and is within 1e-8 of the oracle's solution; each medium system solved
-    alone gives the same bits as in the batch."""
-    specs = [(2, 1, 30, 1, 1, 3, 2), (2, 1, 300, 1, 1, 4, 1), (2, 2, 150, 1, 1, 5, 3), (3, 1, 40, 0, 0, 0, 2),
-             (3, 2, 24, 0, 0, 0, 1), (2, 1, 520, 1, 1, 6, 2)]
+    """An uneven batch spanning the three paths: a small system (one CTA),
+    medium ones (2^15 < n k2 <= 2^16: one 8-CTA cluster each -- 2D P1 200^2,
+    2D P2 100^2, 3D P1 36^3, 3D P2 18^3, 2D P1 150^2 with 2 columns) and a
+    large one (the multi-launch loop).  Every column meets Eq. 2 against the
+    oracle's matrix and is within 1e-8 of the oracle's solution; each medium
+    system solved alone gives the same bits as in the batch."""
+    specs = [(2, 1, 30, 1, 1, 3, 2), (2, 1, 200, 1, 1, 4, 1), (2, 2, 100, 1, 1, 5, 1), (3, 1, 36, 0, 0, 0, 1),
+             (3, 2, 18, 0, 0, 0, 1), (2, 1, 150, 1, 1, 7, 2), (2, 1, 520, 1, 1, 6, 2)]
     mats, Bs, refs, tiers = [], [], [], []
     rng = np.random.default_rng(31)
     for dim, deg, cells, jit, dm, seed, k in specs:
@@ -162,9 +162,9 @@ def test_cluster_tier_uneven_batch(P, prec):
         Bs.append(d.lift(d.dirichlet(gid, coef, k)))
         refs.append(_oracle_cols(dim, deg, cells, jit, dm, seed, gid, coef, k))
         tiers.append(_tier(d.n_free, k))
-    assert tiers == [1, 2, 2, 2, 2, 0]
+    assert tiers == [1, 2, 2, 2, 2, 2, 0]
     p = P.GB_F64 if prec == "f64" else P.GB_F32_IR
-    Xs, sts = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=400000, persist_off=3)
+    Xs, sts = P.pcg_solve_batched(mats, Bs, tol=TOL, precision=p, max_iter=400000, persist_off=0)
     for X, st, (s, rp, ci, v, Bo, Xo) in zip(Xs, sts, refs):
         assert st["status"] == 0, st
         X = X.cpu().numpy()
@@ -173,16 +173,16 @@ def test_cluster_tier_uneven_batch(P, prec):
             assert rel <= 1.5 * TOL, (j, rel)
             assert O.x_err(Xo[:, j], X[:, j]) <= 1e-8
     for i in (1, 3):
-        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, precision=p, max_iter=400000, persist_off=3)
+        Xa, sa = P.pcg_solve_batched([mats[i]], [Bs[i]], tol=TOL, precision=p, max_iter=400000, persist_off=0)
         assert bool((Xa[0] == Xs[i]).all())
         assert sa[0]["iterations"] == sts[i]["iterations"]
 
 
 def test_cluster_tier_matches_multilaunch(P):
-    """The same medium systems through the cluster kernel (persist_off=3) and
+    """The same medium systems through the cluster kernel (persist_off=0) and
     through the multi-launch loop (persist_off=1): the fp64 iterates agree to
     the solver tolerance and the iteration counts to rounding drift."""
-    specs = [(2, 2, 120, 1, 1, 8, 4), (3, 1, 36, 1, 0, 9, 1)]
+    specs = [(2, 2, 90, 1, 1, 8, 2), (3, 1, 36, 1, 0, 9, 1)]
     mats, Bs = [], []
     rng = np.random.default_rng(41)
     for dim, deg, cells, jit, dm, seed, k in specs:
@@ -191,7 +191,7 @@ def test_cluster_tier_matches_multilaunch(P):
         mats.append(d.to_sell(32, 256))
         Bs.append(d.lift(d.dirichlet(gid, rng.standard_normal((k, O.NCOEF[gid])), k)))
         assert _tier(d.n_free, k) == 2
-    Xc, sc = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=3)
+    Xc, sc = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=0)
     Xm, sm = P.pcg_solve_batched(mats, Bs, tol=TOL, max_iter=400000, persist_off=1)
     for X1, X2, s1, s2 in zip(Xc, Xm, sc, sm):
         assert s1["status"] == 0 and s2["status"] == 0

@@ -146,8 +146,8 @@ def test_boundary_data_from_host(P):
 
 MIX_TIERS = [  # one request per path: one block, the cluster lane (two), the lock-step loop
     (2, 1, 40, 1, 1, 11, 2, O.G_HARMONIC),   # n k2 = 3042: one block
-    (2, 1, 200, 1, 1, 12, 2, O.G_HARMONIC),  # 79202: one cluster
-    (3, 2, 20, 0, 0, 0, 1, O.G_LINEAR),      # 59319: one cluster
+    (2, 1, 200, 1, 1, 12, 1, O.G_HARMONIC),  # 39601: the cluster lane
+    (3, 2, 20, 0, 0, 0, 1, O.G_LINEAR),      # 59319: the cluster lane
     (2, 1, 400, 1, 1, 13, 4, O.G_HARMONIC),  # 636804: lock-step loop
 ]
 
