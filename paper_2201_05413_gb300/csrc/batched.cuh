@@ -689,7 +689,10 @@ static int kw_of(int k) {
 static inline int units_of_rows(int64_t n, int64_t *rows_per_unit) {
     const int64_t chunks = (n + 31) / 32;
     const int64_t units = std::max<int64_t>(1, std::min<int64_t>((chunks + 31) / 32, 2048));
-    const int64_t cpu = (chunks + units - 1) / units;
+    int64_t cpu = (chunks + units - 1) / units;
+    // whole groups of 8 chunks (the 256-row sorting windows of the default
+    // layout), which the wide SpMM hands out to its 8 warps one group at a time
+    if (chunks > 8) cpu = (cpu + 7) / 8 * 8;
     *rows_per_unit = cpu * 32;
     return (int)((chunks + cpu - 1) / cpu);
 }

@@ -56,11 +56,14 @@ template <class TX, int K> struct BspmmOcc {
 // One warp's chunks c0, c0 + cs, ..., c0 + (nc - 1) cs of system S (cs = 1:
 // a contiguous range, streamed as one linear array; cs > 1: the chunks are
 // copied piece by piece, a stage never mixing two chunks' bytes in one copy).
+// rot >= 0 (cs a power of two): chunk i is c0 + i cs + ((rot + i) mod cs)
+// instead, i.e. the warp takes a different position in each group of cs
+// chunks.
 // For each column-step of a chunk the 32 rows are taken in G passes of R
 // rows; in pass q lane l works on row q R + l / G and columns (l mod G) VW ..
 // +VW.  Returns the lane's partial P.Q for its VW columns in dot[].
 template <class TX, class TV, int K>
-__device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int64_t nc, int cs, Tma2Ring<TV> &sm,
+__device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int64_t nc, int cs, int rot, Tma2Ring<TV> &sm,
                                                   uint64_t *bars, bool *timed_out, TX (&dot)[BSlice<TX, K>::VW]) {
     constexpr int SJ = Tma2Cfg<TV>::SJ, NB = Tma2Cfg<TV>::NB;
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW, R = BSlice<TX, K>::R;
@@ -79,6 +82,9 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
 #pragma unroll
     for (int u = 0; u < VW; ++u) dot[u] = TX(0);
     if (nc <= 0) return;
+    auto chunk_of = [&](int64_t i) -> int64_t {
+        return rot < 0 ? c0 + i * cs : c0 + i * cs + ((rot + i) & (int64_t)(cs - 1));
+    };
     TX dcomp[VW];  // compensation of dot (kadd)
 #pragma unroll
     for (int u = 0; u < VW; ++u) dcomp[u] = TX(0);
@@ -88,7 +94,7 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
         nsteps = (__ldg(A.chunk_ptr + c0 + nc) - e0) >> 5;
     } else {
         int64_t t = 0;
-        for (int64_t i = lane; i < nc; i += 32) t += __ldg(A.chunk_w + c0 + i * cs);
+        for (int64_t i = lane; i < nc; i += 32) t += __ldg(A.chunk_w + chunk_of(i));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
         nsteps = t;
@@ -112,7 +118,7 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
                 // the stage's sj steps from the chunks at the cursor, one piece per chunk
                 int filled = 0;
                 while (filled < sj && ic < nc) {
-                    const int64_t c = c0 + ic * cs;
+                    const int64_t c = chunk_of(ic);
                     const int64_t w = __ldg(A.chunk_w + c);
                     const int take = (int)min((int64_t)(sj - filled), w - ioff);
                     if (take > 0) {
@@ -162,7 +168,7 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
     // held one per lane), `left` steps of it still to come
     int64_t tb = 0;
     int ci = -1, left = 0;
-    int wv = (lane < nc) ? __ldg(A.chunk_w + c0 + (int64_t)lane * cs) : 0;
+    int wv = (lane < nc) ? __ldg(A.chunk_w + chunk_of(lane)) : 0;
     int64_t rbase = 0;  // first row of the current chunk
     TX acc[G][VW];
 #pragma unroll
@@ -174,10 +180,10 @@ __device__ __forceinline__ void bspmm_warp_stream(const BSys &S, int64_t c0, int
             if (++ci == 32) {
                 tb += 32;
                 ci = 0;
-                wv = (tb + lane < nc) ? __ldg(A.chunk_w + c0 + (tb + lane) * cs) : 0;
+                wv = (tb + lane < nc) ? __ldg(A.chunk_w + chunk_of(tb + lane)) : 0;
             }
             left = __shfl_sync(FULL, wv, ci);
-            rbase = (c0 + (tb + ci) * cs) * 32;
+            rbase = chunk_of(tb + ci) * 32;
             if (left == 0 && tb + ci < nc) {  // an all-empty chunk: its rows of Q are zero
                 TX z[VW];
 #pragma unroll
@@ -325,19 +331,21 @@ __global__ void __launch_bounds__(NT, (BspmmOcc<TX, K>::blocks))
     constexpr int G = BSlice<TX, K>::G, VW = BSlice<TX, K>::VW;
     TX dot[VW];
     if (BSPMM_INTERLEAVE && G > 1 && sizeof(TX) == 4) {
-        // fp32 rows of wide P blocks (G lanes per row): warp w takes chunks
-        // uc0 + w, uc0 + w + 8, ..., so the block's 8 warps work on
-        // neighbouring chunks (one sorting window of 256 rows at a time) and
-        // gather overlapping sets of P rows (2D P2 1024^2, k = 32: 0.870
-        // against 0.896 ms per launch; fp64, bound by its FMA rate, keeps the
-        // contiguous ranges: 0.85 against 0.94 ms at k = 8)
-        const int64_t w0 = uc0 + warp;
-        const int64_t nc = w0 < uc1 ? (uc1 - w0 + TMA_WARPS - 1) / TMA_WARPS : 0;
-        bspmm_warp_stream<TX, TV, K>(S, w0, nc, TMA_WARPS, bufs[warp], &bars[NB * warp], &timed_out, dot);
+        // fp32 rows of wide P blocks (G lanes per row): the block's 8 warps
+        // work on the 8 chunks of one sorting window (256 rows) at a time,
+        // so they gather overlapping sets of P rows, and warp w takes chunk
+        // (w + m) mod 8 of the unit's m-th window: the sort puts a window's
+        // longest rows in its first chunk, and the rotation gives every warp
+        // each position once per 8 windows, so the warps finish together
+        // (2D P2, k = 32: 0.773 against 0.916 ms with contiguous ranges at
+        // 1024^2, 2.69 against 3.34 ms at 2048^2)
+        int64_t nc = 0;
+        while (nc < cpu && uc0 + nc * TMA_WARPS + ((warp + nc) & (TMA_WARPS - 1)) < uc1) ++nc;
+        bspmm_warp_stream<TX, TV, K>(S, uc0, nc, TMA_WARPS, warp, bufs[warp], &bars[NB * warp], &timed_out, dot);
     } else {
         const int64_t cpw = (cpu + TMA_WARPS - 1) / TMA_WARPS;
         const int64_t wc0 = min(uc1, uc0 + warp * cpw), wc1 = min(uc1, wc0 + cpw);
-        bspmm_warp_stream<TX, TV, K>(S, wc0, wc1 - wc0, 1, bufs[warp], &bars[NB * warp], &timed_out, dot);
+        bspmm_warp_stream<TX, TV, K>(S, wc0, wc1 - wc0, 1, -1, bufs[warp], &bars[NB * warp], &timed_out, dot);
     }
     if (timed_out && lane == 0) atomicExch(&G_->err, 1);
     // per-column unit sums in a fixed order: the lanes of a column inside the
