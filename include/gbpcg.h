@@ -283,7 +283,16 @@ typedef struct PcgOptions {
                               power of two >= k) are solved whole by one CTA each in a single
                               persistent launch, and systems with n * k2 <= 65536 by one
                               thread-block cluster of 8 CTAs each in another; 1 = every system in
-                              the multi-launch loop; 2 = the CTA-local tier only */
+                              the multi-launch loop; 2 = the CTA-local tier only; 3 = as 0, and
+                              systems with n * k2 <= 262144 by one group of CTAs each (about one
+                              CTA per 2048 rows x k2, a power of two) in one cooperative launch
+                              per group size, whose group exchanges are bounded waits
+                              (GB_TIMEOUT if one runs out).
+                              pcg_solve (GB_F64, Jacobi, CG): 0 = a system of n <= 8192 rows is
+                              solved whole by one 8-CTA cluster in one launch; 3 = one group of
+                              the grid tier for n <= 262144; 1 = always the multi-kernel loop.
+                              (On GB300 the multi-kernel loop is faster than the grid tier at
+                              every size measured, so the grid tier is not the default.) */
     int32_t precond;       /* GB_PC_JACOBI (0, default) or GB_PC_BLOCK_JACOBI */
     int32_t method;        /* GB_CG (0, default) or GB_BICGSTAB (pcg_solve, GB_F64, C = 32) */
 } PcgOptions;
@@ -484,6 +493,19 @@ int pcg_batched_autotune_width(const gb_sell *A, const double *d_B, int k, int p
  * runs out -- with *h_waited_ms set (may be NULL).  The device stays usable
  * afterwards.  Allocates 16 bytes with cudaMalloc; synchronises `stream`. */
 int gbpcg_wait_selftest(double limit_ms, void *stream, double *h_waited_ms);
+
+/* Diagnostic entry point (no counterpart in the paper): exercises, on the
+ * GPU, the bounded wait of the grid-tier persistent kernel's group exchange
+ * (each block of a group publishes its partial sums and an exchange number in
+ * a slot of global memory and waits until every block's slot shows the same
+ * exchange).  The grid kernel runs with an empty system list and one block of
+ * a group of two, so the second block's number never appears; the wait gives
+ * up after limit_ms milliseconds (0 < limit_ms <= 2000), sets the kernel's
+ * error word and returns, and the call returns GB_TIMEOUT -- what a solve
+ * reports when a group exchange wait runs out -- with the kernel's duration
+ * in *h_waited_ms (may be NULL).  The device stays usable afterwards.
+ * Allocates a few KB with cudaMalloc; synchronises `stream`. */
+int gbpcg_grid_wait_selftest(double limit_ms, void *stream, double *h_waited_ms);
 
 #ifdef __cplusplus
 }

@@ -323,6 +323,13 @@ def wait_selftest(limit_ms=20.0, stream=None):
     return rc, waited.value
 
 
+def grid_wait_selftest(limit_ms=20.0, stream=None):
+    """gbpcg_grid_wait_selftest: (status code, milliseconds the grid kernel ran)."""
+    waited = C.c_double(0.0)
+    rc = G.lib().gbpcg_grid_wait_selftest(float(limit_ms), G.stream_ptr(stream), C.byref(waited))
+    return rc, waited.value
+
+
 class Server:
     """serve_create / serve_submit / serve_poll: a continuous-batching solve
     server.  Host result buffers (numpy, n_free x k) are kept here until the

@@ -18,6 +18,8 @@
 // residual B - A X, convergence test and update X += ||r_j|| D_j in fp64;
 // GB_F32_RU keeps one fp32 recurrence per column and makes fp64 reliable
 // updates (X += D, R = B - A X, residual replacement) every 10x decrease.
+#include <map>
+
 #include "batched.cuh"
 
 
@@ -264,7 +266,9 @@ static int setup_batch(Batch &b, int nsys, const gb_sell *const *A, const double
 // initial residuals already formed): fp64 CG for fp64 batches, fp32 correction
 // solves in fp64 refinement otherwise.  tier 1: one block per system
 // (k_bpersist); tier 2: one cluster of CLUSTER_CS blocks per system
-// (k_bcluster), as many clusters as the SMs hold side by side.
+// (k_bcluster), as many clusters as the SMs hold side by side; tier 3: one
+// group of G blocks per system (k_bgrid, a cooperative launch), as many
+// groups as the device holds.  Returns 1 when tier 3 cannot be resident.
 static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions &o, bool ir, cudaStream_t st,
                        int tier = 1) {
     int *d_list = nullptr, *d_next = nullptr;
@@ -277,6 +281,23 @@ static int run_persist(Batch &b, const std::vector<int> &list, const PcgOptions 
     po.inner_tol = ir ? std::min(o.inner_tol, 1e-4) : 0.0;
     po.maxit = o.max_iter;
     po.max_outer = ir ? o.max_outer : 50;
+    if (tier == 3) {
+        // `list` holds systems of one group size G (the caller buckets them):
+        // groups of G blocks of one cooperative launch
+        const int res = ir ? grid_resident_blocks<float>() : grid_resident_blocks<double>();
+        if (res <= 0) return 1;
+        const int G = grid_blocks_for(b.h[list[0]].A.n, kw_of(b.h[list[0]].k), res);
+        const int groups = (int)std::min<size_t>(list.size(), (size_t)std::max(1, res / G));
+        char *ws = nullptr;
+        const size_t wb = grid_ws_bytes(groups, G);
+        GB_TRY(b.take(&ws, wb));
+        GB_CHECK_CUDA(cudaMemsetAsync(ws, 0, wb, st));
+        int *d_err = nullptr;
+        if (ir) GB_TRY(launch_grid<float>(b.d_sys, d_list, (int)list.size(), d_next, G, groups, ws, po, st, &d_err));
+        else GB_TRY(launch_grid<double>(b.d_sys, d_list, (int)list.size(), d_next, G, groups, ws, po, st, &d_err));
+        b.grid_err.push_back(d_err);
+        return GB_OK;
+    }
     ::gb::count_launches(1);
     if (tier == 2) {
         const int nclu = (int)std::min<size_t>(list.size(), (size_t)std::max(1, num_sms() / CLUSTER_CS));
@@ -342,20 +363,44 @@ extern "C" int pcg_solve_batched(int nsys, const gb_sell *const *A, const double
     // launch for all of them; medium ones by the cluster kernel, one launch
     // for all of them; the loops below then find them converged (or take
     // over the columns they left above tol)
-    std::vector<int> plist, clist;
+    std::vector<int> plist, clist, glist;
     for (int s = 0; s < nsys; ++s) {
         const int tier = o.persist_off == 1 ? 0 : persist_tier(A[s]->n, k[s]);
         if (tier == 1) plist.push_back(s);
         else if (tier == 2 && o.persist_off != 2) clist.push_back(s);
+        else if (tier == 3 && o.persist_off == 3) glist.push_back(s);
+    }
+    if (!glist.empty()) {
+        // one cooperative launch per group size (a system's group size depends
+        // on its own size only, so its result does not depend on the batch)
+        const int res = ir ? grid_resident_blocks<float>() : grid_resident_blocks<double>();
+        std::map<int, std::vector<int>> by_g;
+        for (int s : glist) by_g[grid_blocks_for(A[s]->n, kw_of(k[s]), std::max(res, 1))].push_back(s);
+        for (auto &kv : by_g) {
+            const int grc = res > 0 ? run_persist(b, kv.second, o, ir, st, 3) : 1;
+            if (grc == 1) { glist.clear(); break; }  // not resident on this device: the loop takes them
+            GB_TRY(grc);
+        }
     }
     if (!clist.empty()) GB_TRY(run_persist(b, clist, o, ir, st, 2));
     for (int s : clist) plist.push_back(s);
+    const size_t nsmall = plist.size() - clist.size();
+    for (int s : glist) plist.push_back(s);
     if (!plist.empty()) {
-        if ((int)plist.size() > (int)clist.size()) {
-            std::vector<int> small(plist.begin(), plist.end() - clist.size());
+        if (nsmall > 0) {
+            std::vector<int> small(plist.begin(), plist.begin() + nsmall);
             GB_TRY(run_persist(b, small, o, ir, st, 1));
         }
         GB_TRY(pull_cols(b, hc, st));
+        for (int *ep : b.grid_err) {
+            int herr = 0;
+            GB_CHECK_CUDA(cudaMemcpyAsync(&herr, ep, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GB_CHECK_CUDA(cudaStreamSynchronize(st));
+            if (herr) {
+                set_error("pcg_solve_batched: a grid-tier group barrier wait ran out");
+                return GB_TIMEOUT;
+            }
+        }
         std::vector<BSys> hs(nsys);
         GB_CHECK_CUDA(cudaMemcpyAsync(hs.data(), b.d_sys, sizeof(BSys) * nsys, cudaMemcpyDeviceToHost, st));
         GB_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -620,5 +665,180 @@ extern "C" int pcg_batched_autotune_width(const gb_sell *A, const double *d_B, i
     }
     for (int wi = 0; wi < 6 && h_ms; ++wi)
         if (widths[wi] > k) h_ms[wi] = 0.0;
+    return GB_OK;
+}
+
+// ------------------------------------------------------------- grid tier --
+// One fp64 system (one right-hand side) solved whole by one persistent
+// launch: one thread-block cluster (n <= 2^16, hardware cluster barriers) or
+// one group of the grid tier (a cooperative launch).  A single workspace
+// allocation (stream-ordered), the permuted b and x0 gathered, the launch --
+// which forms r = b - A x0, ||b|| and the threshold itself and runs the CG
+// rounds with true-residual restarts --, x scattered back, and one copy of
+// the column state to the host.  Returns 1 (nothing done) when the grid
+// kernel cannot be resident on this device.
+int gb::grid_solve_single(const gb_sell *M, const double *d_b, double *d_x, const PcgOptions &o, cudaStream_t st,
+                          PcgStats *stats) {
+    const int64_t n = M->n;
+    const bool cluster = n <= GB_CLUSTER_SINGLE_MAX && o.persist_off != 3;
+    const int res = cluster ? CLUSTER_CS : grid_resident_blocks<double>();
+    if (res <= 0) return 1;
+    const int G = cluster ? CLUSTER_CS : grid_blocks_for(n, 1, res);
+    // workspace: [BSys | cd | ci | cs | list, next | grid ws | B64 X64 R64 P Q]
+    const size_t o_sys = 0;
+    const size_t o_cd = o_sys + align256(sizeof(BSys));
+    const size_t o_ci = o_cd + align256(sizeof(double) * 10 * KMAX);
+    const size_t o_cs = o_ci + align256(sizeof(long long) * KMAX);
+    const size_t o_lst = o_cs + align256(sizeof(int) * 2 * KMAX);
+    const size_t o_ws = o_lst + 256;
+    const size_t o_vec = o_ws + grid_ws_bytes(1, G);
+    const size_t bytes = o_vec + 5 * align256(sizeof(double) * (size_t)n);
+    char *ws = nullptr;
+    {
+        const cudaError_t e = cudaMallocAsync((void **)&ws, bytes, st);
+        if (e != cudaSuccess) {
+            set_error("pcg_solve (grid tier): cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA;
+        }
+        count_device_alloc();
+    }
+    struct Free {
+        char *p;
+        cudaStream_t s;
+        ~Free() { if (p) cudaFreeAsync(p, s); }
+    } guard{ws, st};
+    const size_t vb = align256(sizeof(double) * (size_t)n);
+    double *B64 = (double *)(ws + o_vec), *X64 = (double *)(ws + o_vec + vb), *R64 = (double *)(ws + o_vec + 2 * vb);
+    double *P = (double *)(ws + o_vec + 3 * vb), *Q = (double *)(ws + o_vec + 4 * vb);
+    BSys h{};
+    h.A = M->view();
+    h.val = M->val;
+    h.X = X64; h.R = R64; h.P = P; h.Q = Q;
+    h.B64 = B64; h.X64 = X64; h.R64 = R64;
+    double *cd = (double *)(ws + o_cd);
+    h.c.rho = cd; h.c.pq = cd + KMAX; h.c.alpha = cd + 2 * KMAX; h.c.beta = cd + 3 * KMAX;
+    h.c.rr = cd + 4 * KMAX; h.c.bb = cd + 5 * KMAX; h.c.thresh = cd + 6 * KMAX; h.c.scale = cd + 7 * KMAX;
+    h.c.pz = cd + 8 * KMAX; h.c.target = cd + 9 * KMAX;
+    h.c.it = (long long *)(ws + o_ci);
+    h.c.done = (int *)(ws + o_cs);
+    h.c.status = (int *)(ws + o_cs) + KMAX;
+    h.k = 1;
+    h.kw = 1;
+    h.unit0 = 0;
+    h.nunits = 1;
+    h.rows_per_unit = n;
+    h.active = 1;
+    GB_CHECK_CUDA(cudaMemsetAsync(ws, 0, o_vec, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(ws + o_sys, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GB_CHECK_CUDA(cudaEventCreate(&e0));
+    GB_CHECK_CUDA(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evs{e0, e1};
+    GB_CHECK_CUDA(cudaEventRecord(e0, st));
+    const int g = stride_grid(n, 256, 8);
+    ::gb::count_launches(1); k_gather_rows<<<g, 256, 0, st>>>(n, 1, M->perm, d_b, B64);
+    ::gb::count_launches(1); k_gather_rows<<<g, 256, 0, st>>>(n, 1, M->perm, o.x0_zero ? nullptr : d_x, X64);
+    GB_CHECK_CUDA(cudaGetLastError());
+    PersistOpts po{};
+    po.tol = o.tol;
+    po.maxit = o.max_iter;
+    po.max_outer = 50;
+    po.init = 1;
+    po.x0_zero = o.x0_zero ? 1 : 0;
+    int *list = (int *)(ws + o_lst), *next = list + 1;
+    int *d_err = nullptr;
+    if (cluster) {
+        // the grid workspace's error word stays zero: a cluster's barriers are hardware ones
+        d_err = grid_ws_err(ws + o_ws, 1, G);
+        ::gb::count_launches(1);
+        k_bcluster<double><<<CLUSTER_CS, PNT, 0, st>>>((BSys *)(ws + o_sys), list, 1, next, po);
+        GB_CHECK_CUDA(cudaGetLastError());
+    } else {
+        GB_TRY(launch_grid<double>((BSys *)(ws + o_sys), list, 1, next, G, 1, ws + o_ws, po, st, &d_err));
+    }
+    ::gb::count_launches(1); k_scatter_rows<<<g, 256, 0, st>>>(n, 1, M->perm, X64, d_x);
+    GB_CHECK_CUDA(cudaGetLastError());
+    GB_CHECK_CUDA(cudaEventRecord(e1, st));
+    // column state, the tier's round count and the error word
+    std::vector<char> hb(o_ws);
+    int herr = 0;
+    GB_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws, o_ws, cudaMemcpyDeviceToHost, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CHECK_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const BSys *hs = (const BSys *)(hb.data() + o_sys);
+    const double *hcd = (const double *)(hb.data() + o_cd);
+    const long long it = ((const long long *)(hb.data() + o_ci))[0];
+    const int done = ((const int *)(hb.data() + o_cs))[0];
+    const int status = ((const int *)(hb.data() + o_cs))[KMAX];
+    const double rr = hcd[4 * KMAX], bb = hcd[5 * KMAX];
+    *stats = PcgStats{};
+    stats->iterations = it;
+    stats->restarts = hs->outer > 1 ? hs->outer - 1 : 0;
+    stats->bnorm = std::sqrt(bb);
+    stats->relres = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    stats->solve_ms = ms;
+    stats->kernel_launches = 4;
+    stats->bytes_moved = (double)it * ((double)M->nnz * 12.0 + 7.0 * (double)n * 8.0);
+    if (herr || !done) stats->status = GB_TIMEOUT;
+    else if (bb == 0.0 || stats->relres <= o.tol) stats->status = GB_OK;
+    else if (status == ST_BREAK) stats->status = GB_BREAKDOWN;
+    else if (status == ST_TIMEOUT) stats->status = GB_TIMEOUT;
+    else stats->status = GB_NOT_CONVERGED;
+    if (bb == 0.0) {  // b = 0: x = 0 (the kernel ran no round; X64 holds x0)
+        GB_CHECK_CUDA(cudaMemsetAsync(d_x, 0, sizeof(double) * (size_t)n, st));
+        stats->relres = 0.0;
+    }
+    return GB_OK;
+}
+
+// A group exchange that must run out: one block launched of a group of two,
+// so the second block's exchange number never appears and the first one's
+// wait ends on its time limit -- through the grid kernel itself, with an
+// empty list (no system is touched).
+extern "C" int gbpcg_grid_wait_selftest(double limit_ms, void *stream, double *h_waited_ms) {
+    GB_REQUIRE(limit_ms > 0.0 && limit_ms <= 2000.0, "gbpcg_grid_wait_selftest: limit_ms must be in (0, 2000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int G = 2;
+    const size_t o_ws = 256;
+    const size_t bytes = o_ws + grid_ws_bytes(1, G);
+    char *ws = nullptr;
+    GB_CHECK_CUDA(cudaMalloc((void **)&ws, bytes));
+    count_device_alloc();
+    int *list = (int *)ws, *next = list + 1;
+    GB_CHECK_CUDA(cudaMemsetAsync(ws, 0, bytes, st));
+    PersistOpts po{};
+    po.wait_ns = (unsigned long long)(limit_ms * 1e6);
+    double *gslots = (double *)(ws + o_ws);
+    int *err = grid_ws_err(ws + o_ws, 1, G);
+    BSys *no_sys = nullptr;
+    int nlist = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    // one block launched of a group of two: the barrier's second arrival never comes
+    ::gb::count_launches(1);
+    k_bgrid<double><<<1, PNT, 0, st>>>(no_sys, list, nlist, next, gslots, G, err, po);
+    cudaError_t e = cudaGetLastError();
+    cudaEventRecord(e1, st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ws);
+    if (e != cudaSuccess) { set_error("gbpcg_grid_wait_selftest: %s", cudaGetErrorString(e)); return GB_ECUDA; }
+    if (h_waited_ms) *h_waited_ms = ms;
+    if (herr) {
+        set_error("gbpcg_grid_wait_selftest: the group barrier gave up after %.3f ms", (double)ms);
+        return GB_TIMEOUT;
+    }
     return GB_OK;
 }

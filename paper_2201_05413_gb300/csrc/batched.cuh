@@ -665,6 +665,7 @@ struct Batch {
     double *partials = nullptr;
     std::vector<void *> owned;
     int units = 0;
+    std::vector<int *> grid_err;  // error words of the grid-tier launches
     bool tma = false;  // every system has 32-row chunks: the TMA-streamed SpMM applies
     ClassRanges cls;   // the unit table ordered by width class
     template <class T> int take(T **p, size_t n) {
@@ -695,6 +696,70 @@ static inline int units_of_rows(int64_t n, int64_t *rows_per_unit) {
     if (chunks > 8) cpu = (cpu + 7) / 8 * 8;
     *rows_per_unit = cpu * 32;
     return (int)((chunks + cpu - 1) / cpu);
+}
+
+// ------------------------------------------------------------- grid tier --
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Blocks of k_bgrid<TX> the current device holds at once: the size bound of
+// its cooperative launches (0 if the kernel cannot be resident).
+template <class TX> int grid_resident_blocks() {
+    static int cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bgrid<TX>, PNT, 0) != cudaSuccess) {
+            (void)cudaGetLastError();
+            per_sm = 0;
+        }
+        cache[dev] = per_sm * num_sms();
+    }
+    return cache[dev];
+}
+
+// Blocks per group for n rows with kp columns each: about one block per
+// GB_GRID_ROWS row-columns, rounded up to a power of two and at most the
+// largest power of two the device holds.  A system's group size, and with it
+// the order of its sums, depends on its own size only.
+inline int grid_blocks_for(int64_t n, int kp, int resident) {
+    const int64_t want = (n * kp + GB_GRID_ROWS - 1) / GB_GRID_ROWS;
+    int64_t cap = 1;
+    while (cap * 2 <= resident) cap *= 2;
+    int64_t g = 1;
+    while (g < want && g < cap) g *= 2;
+    return (int)g;
+}
+
+// Bytes of a grid launch's workspace: per group two phases of G exchange
+// slots, then the kernel's error word (grid_ws_err).
+inline size_t grid_ws_bytes(int groups, int G) {
+    return align256(sizeof(double) * 2 * GRID_SLOT * (size_t)G * groups) + 256;
+}
+inline int *grid_ws_err(void *ws, int groups, int G) {
+    return (int *)((char *)ws + align256(sizeof(double) * 2 * GRID_SLOT * (size_t)G * groups));
+}
+
+// One cooperative launch of k_bgrid<TX>: `groups` groups of G blocks over the
+// list (d_next zeroed, ws zeroed: grid_ws_bytes(groups, G)).  *d_err_out
+// receives the address of the error word.
+template <class TX>
+int launch_grid(BSys *d_sys, const int *d_list, int nlist, int *d_next, int G, int groups, void *ws,
+                const PersistOpts &po, cudaStream_t st, int **d_err_out = nullptr) {
+    double *gslots = (double *)ws;
+    int *err = grid_ws_err(ws, groups, G);
+    if (d_err_out) *d_err_out = err;
+    PersistOpts o = po;
+    void *args[] = {(void *)&d_sys, (void *)&d_list, (void *)&nlist, (void *)&d_next, (void *)&gslots,
+                    (void *)&G,     (void *)&err,    (void *)&o};
+    ::gb::count_launches(1);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_bgrid<TX>, dim3((unsigned)(groups * G)),
+                                                      dim3(PNT), args, 0, st);
+    if (e != cudaSuccess) {
+        set_error("grid-tier launch (%d groups of %d blocks): %s", groups, G, cudaGetErrorString(e));
+        return GB_ECUDA;
+    }
+    return GB_OK;
 }
 
 // Widest width class (0: k = 1 .. 5: k <= 32) that takes the TMA-streamed SpMM;

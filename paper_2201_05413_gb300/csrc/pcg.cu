@@ -1092,6 +1092,26 @@ extern "C" int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const
                    o.precision == GB_BF16_IR,
                "pcg_solve: GB_PC_BLOCK_JACOBI with GB_F64, GB_F32_IR or GB_BF16_IR only");
     cudaStream_t st = (cudaStream_t)stream;
+    if (o.precision == GB_F64 && o.method == GB_CG && o.precond == GB_PC_JACOBI &&
+        ((o.persist_off == 0 && A->n <= GB_CLUSTER_SINGLE_MAX) || (o.persist_off == 3 && A->n <= GB_GRID_SINGLE_MAX))) {
+        // a system this small is latency-bound in the loop of three grid-wide
+        // launches per iteration and in its per-solve set-up: one persistent
+        // launch (one thread-block cluster) solves it whole; persist_off = 3
+        // asks for a group of the grid tier up to 2^18 rows
+        const int rc = grid_solve_single(A, d_b, d_x, o, st, stats);
+        if (rc != 1) {
+            if (rc != GB_OK) return rc;
+            if (stats->status != GB_OK) {
+                set_error("pcg_solve: %s after %lld iterations (relres %.3e)",
+                          stats->status == GB_BREAKDOWN ? "breakdown"
+                          : stats->status == GB_TIMEOUT ? "a persistent-kernel barrier wait ran out"
+                                                        : "not converged",
+                          (long long)stats->iterations, stats->relres);
+                return stats->status;
+            }
+            return GB_OK;
+        }
+    }
     Work w;
     w.mem = Mem(nullptr, st);
     const int64_t n = A->n;

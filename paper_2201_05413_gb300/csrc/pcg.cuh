@@ -106,4 +106,26 @@ __device__ __forceinline__ void stop(PcgScal *S, int status) {
     if (S->use_cond) cudaGraphSetConditional(S->cond, 0);
 }
 
+// Rows (times the column power of two) per block of a grid-tier group, and
+// the largest single system pcg_solve hands to the grid tier when asked to
+// (PcgOptions.persist_off = 3).
+#ifndef GB_GRID_ROWS
+#define GB_GRID_ROWS 2048
+#endif
+#ifndef GB_GRID_SINGLE_MAX
+#define GB_GRID_SINGLE_MAX (1 << 18)
+#endif
+// the largest single system pcg_solve solves by one thread-block cluster by
+// default (64^2 P1, 3969 rows: 1.52 against 2.30 ms per solve in the
+// multi-kernel loop; at 16129 rows the loop is faster, 14.0 against 20.1 ms)
+#ifndef GB_CLUSTER_SINGLE_MAX
+#define GB_CLUSTER_SINGLE_MAX (1 << 13)
+#endif
+
+// fp64 Jacobi-PCG of one system by one group of the grid-tier persistent
+// kernel (batched.cu): returns GB_OK with *stats filled, an error code, or 1
+// when the tier is not available (the caller takes the multi-kernel loop).
+int grid_solve_single(const gb_sell *M, const double *d_b, double *d_x, const PcgOptions &o, cudaStream_t st,
+                      PcgStats *stats);
+
 }  // namespace gb

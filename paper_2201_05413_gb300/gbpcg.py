@@ -159,6 +159,7 @@ _SIGS = {
     "pcg_solve_batched": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                     C.POINTER(C.c_int), C.POINTER(PcgOptions), _P, C.POINTER(PcgStats)]),
     "gbpcg_wait_selftest": (C.c_int, [C.c_double, _P, C.POINTER(C.c_double)]),
+    "gbpcg_grid_wait_selftest": (C.c_int, [C.c_double, _P, C.POINTER(C.c_double)]),
     "pcg_batched_autotune_width": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pcg_batched_kernel_times": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_int), C.c_int,
                                            C.c_int, _P, C.POINTER(C.c_double)]),

@@ -36,6 +36,22 @@ def test_bounded_wait_runs_out_and_device_stays_usable(P):
         P.gbpcg.check(P.gbpcg.lib().gbpcg_wait_selftest(0.0, None, None), "bad limit")
 
 
+def test_grid_barrier_wait_runs_out_and_device_stays_usable(P):
+    """The grid tier's group barrier with one arrival that never comes: the
+    wait gives up after its limit, the call reports GB_TIMEOUT, and a solve
+    on the same tier right after succeeds."""
+    rc, waited = P.grid_wait_selftest(20.0)
+    assert rc == P.gbpcg.GB_TIMEOUT
+    assert 20.0 <= waited < 1000.0, waited
+    d = P.FemSystem(2, 1, 64, 0, 0, 0)
+    A = d.to_sell(32, 256)
+    b = d.lift(d.dirichlet(O.G_SIN_SINH))[:, 0]
+    x, st = A.solve(b, tol=1e-10, persist_off=3)  # one persistent grid-tier launch
+    assert st["status"] == 0 and st["relres"] <= 1e-10 and st["kernel_launches"] <= 4
+    with pytest.raises(P.GbError):
+        P.gbpcg.check(P.gbpcg.lib().gbpcg_grid_wait_selftest(0.0, None, None), "bad limit")
+
+
 class _FailingAllocator:
     """cudaMalloc-backed gb_allocator that returns NULL from its n-th call on."""
 

@@ -48,8 +48,9 @@ def _solve_both(P, dim, deg, cells, jit, dm, seed, gid, coef=None, C=32, sigma=2
     (3, 2, 10, 0, 0, 0, O.G_X2_Y2_2Z2),
     (3, 1, 20, 1, 0, 2, O.G_X2_Y2_2Z2),     # jittered 3D P1: no closed form, oracle solve
 ])
-def test_fp64_pcg_matches_oracle(P, case):
-    d, s, xd, xo, st, ito, relres = _solve_both(P, *case)
+@pytest.mark.parametrize("persist_off", [0, 1, 3])
+def test_fp64_pcg_matches_oracle(P, case, persist_off):
+    d, s, xd, xo, st, ito, relres = _solve_both(P, *case, persist_off=persist_off)
     assert st["status"] == 0
     assert st["relres"] <= TOL and relres <= 1.5 * TOL
     assert O.x_err(xo, xd) <= XERR
@@ -130,9 +131,9 @@ def test_graph_and_direct_launch_identical(P):
     d = P.FemSystem(2, 2, 30, 1, 1, 3)
     A = d.to_sell(32, 64)
     b = d.lift(d.dirichlet(1))[:, 0]
-    x1, s1 = A.solve(b, use_graph=1)
-    x2, s2 = A.solve(b, use_graph=0, check_every=7)
-    x3, s3 = A.solve(b, use_graph=1)
+    x1, s1 = A.solve(b, use_graph=1, persist_off=1)
+    x2, s2 = A.solve(b, use_graph=0, check_every=7, persist_off=1)
+    x3, s3 = A.solve(b, use_graph=1, persist_off=1)
     assert s1["iterations"] == s2["iterations"] == s3["iterations"]
     assert bool((x1 == x2).all()) and bool((x1 == x3).all())
 
