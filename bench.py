@@ -677,7 +677,8 @@ def run_serving(nreq, seed=4):
     fp64 recurrences (so batching and precision show apart).  (2) The same
     requests arriving as a Poisson stream at 0.8 x the fp32 saturated
     throughput: p50/p99 latency (submit to result).  (3) The same requests one
-    at a time in fp64 (pcg_solve_batched per request): throughput, and the
+    at a time in fp64 (pcg_solve for k = 1, pcg_solve_batched for the k
+    columns of a request otherwise): throughput, and the
     p50/p99 latency a single FIFO server with these measured service times
     would give under the same arrival stream."""
     import numpy as np
@@ -722,7 +723,9 @@ def run_serving(nreq, seed=4):
     srv.close()
     lat2 = np.array([res2[t][0]["latency_ms"] for t in ts2])
     ok2 = sum(1 for t in ts2 if res2[t][0]["status"] == 0)
-    # one at a time, fp64: measured service time of each request
+    # one at a time, fp64: measured service time of each request, solved by the
+    # library's fastest single-request path (pcg_solve for one right-hand side,
+    # the blocked multi-RHS solve of its k columns otherwise)
     service = []
     for r in reqs:
         torch.cuda.synchronize()
@@ -730,7 +733,10 @@ def run_serving(nreq, seed=4):
         d = P.FemSystem(r["dim"], r["degree"], r["cells"], r["jitter"], r["diag_mode"], r["seed"])
         A = d.to_sell(32, 256, P.GB_VAL_F64)
         B = d.lift(d.dirichlet(r["gid"], r["coef"], r["k"]))
-        P.pcg_solve_batched([A], [B], tol=TOL, max_iter=2000000)
+        if r["k"] == 1:
+            A.solve(B[:, 0], tol=TOL, max_iter=2000000)
+        else:
+            P.pcg_solve_batched([A], [B], tol=TOL, max_iter=2000000)
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t3)
         del A, B, d
