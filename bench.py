@@ -746,7 +746,13 @@ def run_serving(nreq, seed=4):
         done = max(done, ta) + sv
         lat3.append(1e3 * (done - ta))
     lat3 = np.array(lat3)
-    return {"requests": nreq, "of_10000": round(nreq / 10000, 4), "seed": seed,
+    per_req = []
+    for r, l2, sv in zip(reqs, lat2, service):
+        side = r["degree"] * r["cells"] - 1
+        per_req.append({"dim": r["dim"], "degree": r["degree"], "cells": r["cells"], "k": r["k"],
+                        "n": side ** r["dim"], "poisson_latency_ms": round(float(l2), 1),
+                        "alone_f64_ms": round(1e3 * sv, 1)})
+    return {"requests": nreq, "of_10000": round(nreq / 10000, 4), "seed": seed, "per_request": per_req,
             "mix": "cfg5 generator (70% 2D jittered n in [32,1024], 30% 3D Kuhn n in [16,128], P1/P2, k 1-8), "
                    "mem budget 40 GB, up to 64 resident",
             "saturated_f32_ru": sat32, "saturated_f64": sat64,

@@ -311,7 +311,14 @@ typedef struct PcgStats {
                                      refinement stalled above tol (0 if none) */
 } PcgStats;
 
-/* Solves A x = b for one right-hand side.  d_b, d_x: n doubles (x in: x0).
+/* Solves A x = b for one right-hand side (Sec. 2.1: preconditioned Krylov
+ * solve; Eq. 2: stop at ||b - A x|| <= tol ||b||, confirmed on the true
+ * residual).  d_b, d_x: n doubles in the original free-dof order (x in: x0
+ * unless x0_zero).  GB_F64 Jacobi-CG: the CG loop is a CUDA-graph while-node
+ * of three kernels per iteration, or, for n <= 8192 (persist_off = 0), one
+ * launch of a persistent kernel on one 8-CTA thread-block cluster that forms
+ * the residual and runs every iteration (its memory comes from the
+ * stream-ordered pool); persist_off = 1 always takes the graph loop.
  * Synchronises `stream` (convergence polling and statistics). */
 int pcg_solve(const gb_sell *A, const double *d_b, double *d_x, const PcgOptions *opt,
               void *stream, PcgStats *stats);

@@ -86,7 +86,9 @@ def test_noalloc_warm_start_matches_pcg_solve(P):
 
 
 def test_noalloc_second_system_after_first(P):
-    """A smaller system after a larger one: nothing stale from the first call leaks in."""
+    """A smaller system after a larger one: nothing stale from the first call
+    leaks in; the second result is also checked against the oracle."""
+    import oracle as O
     d1 = P.FemSystem(2, 1, 400, 1, 1, 1)
     d2 = P.FemSystem(2, 2, 30, 1, 1, 2)
     for d in (d1, d2):
@@ -95,6 +97,10 @@ def test_noalloc_second_system_after_first(P):
         x_ref, _ = A.solve(b, tol=TOL)
         rc, x, st = _noalloc(P, A, b, tol=TOL)
         assert rc == 0 and _xerr(x_ref, x) <= XERR
+    s = O.System(2, 2, 30, 1, 1, 2).assemble()
+    rp, ci, v = s.k_ii()
+    xo, _, _, _ = O.pcg(rp, ci, v, s.lift(s.eval_g(O.G_X2_Y2))[:, 0], tol=1e-13)
+    assert O.x_err(xo, x.cpu().numpy()) <= XERR
 
 
 def test_noalloc_rejects_oversized_and_other_precisions(P):
