@@ -1,9 +1,11 @@
 // serve.cu -- continuous-batching solve server (serve_create / submit / poll).
 //
-// A server thread owns two streams.  On the main stream it advances every
-// resident request ("slot": its matrix, right-hand sides and Krylov state stay
-// on the device) by a chunk of CG iterations in shared launches -- the batched
-// kernels of batched.cuh over a table of the iterating slots.  While a chunk
+// A server thread owns a side stream and two lane streams.  On each lane's
+// stream it advances that lane's resident requests ("slots": a slot's matrix,
+// right-hand sides and Krylov state stay on the device) by a chunk of CG
+// iterations in shared launches -- the batched kernels of batched.cuh over a
+// table of the lane's iterating slots; medium requests (n k2 <= 2^20) have a
+// lane of their own, so they do not iterate at the pace of the largest ones.  While a chunk
 // runs, pending requests are admitted on the side stream as slots and memory
 // allow: device assembly, SELL conversion, Dirichlet lift and the start of
 // their recurrences, allocated from a stream-ordered pool and charged against
@@ -59,6 +61,7 @@ struct Slot {
     int k = 1, kw = 1;
     bool ru = true;
     int ptier = 0;  // persistent tier solving it (1 one block, 2 one cluster), 0 = the lock-step loop
+    int lane = 0;   // lock-step lane: 1 for n k2 <= 2^GB_SERVE_MEDIUM_LOG2, else 0
     double *B64 = nullptr, *X64 = nullptr, *R64 = nullptr;
     void *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
     double *cd = nullptr;
@@ -84,9 +87,24 @@ struct Slot {
 struct gb_server {
     ServeOptions opt{};
     int dev = 0;
-    cudaStream_t main_st = nullptr, side_st = nullptr;
-    cudaEvent_t ev = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing of a chunk (adaptive chunk length)
+    // One lock-step loop per lane, on a stream of its own with its own system
+    // table: lane 0 takes the requests above 2^GB_SERVE_MEDIUM_LOG2 elements
+    // (n k2) and the service steps, lane 1 the medium ones, so that a medium
+    // request's iterations do not wait for the largest requests' iterations.
+    struct Lane {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // timing of a chunk (adaptive chunk length)
+        gb::BSys *d_sys = nullptr;
+        int *d_unit_sys = nullptr;
+        gb::BGlobal *d_G = nullptr;
+        double *d_partials = nullptr;
+        size_t cap_umap = 0, cap_part = 0;
+        int ips = 16;  // iterations of the next chunk (adaptive mode)
+    };
+    static constexpr int NLANES = 2;
+    Lane ln[NLANES];
+    cudaStream_t side_st = nullptr;
     struct PLaunch {  // one persistent launch, on a stream of its own
         std::vector<gb::Slot *> slots;
         gb::BSys *d_tab = nullptr;
@@ -95,7 +113,6 @@ struct gb_server {
         cudaEvent_t done = nullptr;
     };
     std::vector<std::unique_ptr<PLaunch>> plaunch;
-    int ips = 16;                            // iterations of the next chunk (adaptive mode)
     std::thread th;
     std::mutex mu;
     std::condition_variable cv;
@@ -110,12 +127,7 @@ struct gb_server {
     std::unordered_map<void *, size_t> sizes;
     gb_allocator alloc{};  // what the slots' assembly and SELL build allocate through (srv_alloc)
     gb_allocator user{};   // the caller's allocator (serve_create), or none: the stream-ordered pool
-    // table buffers (main stream)
-    gb::BSys *d_sys = nullptr;
-    int *d_unit_sys = nullptr, *d_mask = nullptr;
-    gb::BGlobal *d_G = nullptr;
-    double *d_partials = nullptr;
-    size_t cap_umap = 0, cap_part = 0;
+    int *d_mask = nullptr;  // column masks of the service step (lane 0's stream)
     // single-slot buffers used while admitting (side stream)
     gb::BSys *d_sys1 = nullptr;
     int *d_unit1 = nullptr, *d_mask1 = nullptr;
@@ -256,6 +268,21 @@ static int serve_persist_tier(int64_t n, int k, bool ru, bool cluster_lane) {
     return 0;
 }
 
+// Lock-step lane of a request: medium requests (n k2 <= 2^GB_SERVE_MEDIUM_LOG2)
+// iterate in lane 1, larger ones in lane 0, each lane in launches of its own
+// on its own stream, so a medium request advances at the pace of the medium
+// requests' iterations rather than the largest requests' (cfg5 mix, 160
+// requests: medium requests waited 16 x their one-at-a-time time at the
+// median with a single lane).
+#ifndef GB_SERVE_MEDIUM_LOG2
+#define GB_SERVE_MEDIUM_LOG2 20
+#endif
+static int serve_lane(int64_t n, int k) {
+    int kp = 1;
+    while (kp < k) kp <<= 1;
+    return n * kp <= ((int64_t)1 << GB_SERVE_MEDIUM_LOG2) ? 1 : 0;
+}
+
 // --------------------------------------------------------------- admit --
 static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
     const bool ru = s->opt.precision != GB_F64;
@@ -361,6 +388,7 @@ static int admit(gb_server *s, SReq &q, std::unique_ptr<Slot> &out) {
         target[j] = 0.25 * s->opt.tol * s->opt.tol * bb[j];
     }
     L.ptier = serve_persist_tier(L.n, L.k, ru, s->opt.cluster_lane != 0);
+    L.lane = serve_lane(L.n, L.k);
     if (L.ptier) {
         // small or medium request: solved whole by one block (or one cluster)
         // of the next persistent launch (launch_persistent), not in the
@@ -434,7 +462,7 @@ static void retire(gb_server *s, Slot &L, int status) {
 // fp64 test per column, then either final or re-armed (replacement / restart).
 static int service(gb_server *s, std::vector<Slot *> &sv) {
     if (sv.empty()) return GB_OK;
-    cudaStream_t st = s->main_st;
+    cudaStream_t st = s->ln[0].st;
     const bool ru = s->opt.precision != GB_F64;
     std::vector<BSys> tab;
     std::vector<int> umap;
@@ -442,13 +470,13 @@ static int service(gb_server *s, std::vector<Slot *> &sv) {
         tab.push_back(desc_of(*sv[i], (int)umap.size()));
         for (int u = 0; u < sv[i]->units; ++u) umap.push_back((int)i);
     }
-    GB_TRY(grow(s, &s->d_partials, &s->cap_part, umap.size() * 3 * KMAX, st));
-    GB_TRY(grow(s, &s->d_unit_sys, &s->cap_umap, umap.size(), st));
+    GB_TRY(grow(s, &s->ln[0].d_partials, &s->ln[0].cap_part, umap.size() * 3 * KMAX, st));
+    GB_TRY(grow(s, &s->ln[0].d_unit_sys, &s->ln[0].cap_umap, umap.size(), st));
     std::vector<int> mask(tab.size() * KMAX, 0);
     for (size_t i = 0; i < sv.size(); ++i)
         for (int j = 0; j < sv[i]->k; ++j) mask[i * KMAX + j] = sv[i]->fin[j] ? 0 : 1;
-    GB_CHECK_CUDA(cudaMemcpyAsync(s->d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, st));
-    GB_CHECK_CUDA(cudaMemcpyAsync(s->d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(s->ln[0].d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, st));
+    GB_CHECK_CUDA(cudaMemcpyAsync(s->ln[0].d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, st));
     GB_CHECK_CUDA(cudaMemcpyAsync(s->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
     const int U = (int)umap.size();
     if (ru) {
@@ -458,10 +486,10 @@ static int service(gb_server *s, std::vector<Slot *> &sv) {
             GB_CHECK_CUDA(cudaMemcpyAsync(L->c.scale, one.data(), sizeof(double) * KMAX, cudaMemcpyHostToDevice, st));
         }
         ::gb::count_launches(1);
-        k_bcorrect<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_mask);
+        k_bcorrect<<<U, NT, 0, st>>>(s->ln[0].d_sys, s->ln[0].d_unit_sys, s->d_mask);
     }
     ::gb::count_launches(1);
-    k_bresid<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, 0, 0, s->opt.tol);
+    k_bresid<<<U, NT, 0, st>>>(s->ln[0].d_sys, s->ln[0].d_unit_sys, s->ln[0].d_partials, 0, 0, s->opt.tol);
     GB_CHECK_CUDA(cudaGetLastError());
     // decide per column
     bool any = false;
@@ -501,12 +529,12 @@ static int service(gb_server *s, std::vector<Slot *> &sv) {
         GB_CHECK_CUDA(cudaMemcpyAsync(s->d_mask, mask.data(), sizeof(int) * mask.size(), cudaMemcpyHostToDevice, st));
         if (ru) {
             ::gb::count_launches(2);
-            k_breplace<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, s->d_mask, 0.01);
-            k_breplace_p<<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_mask);
+            k_breplace<<<U, NT, 0, st>>>(s->ln[0].d_sys, s->ln[0].d_unit_sys, s->ln[0].d_partials, s->d_mask, 0.01);
+            k_breplace_p<<<U, NT, 0, st>>>(s->ln[0].d_sys, s->ln[0].d_unit_sys, s->d_mask);
         } else {
             // fp64 recurrence: restart from the true residual (R64 already holds it)
             ::gb::count_launches(1);
-            k_bstart<double><<<U, NT, 0, st>>>(s->d_sys, s->d_unit_sys, s->d_partials, s->d_mask);
+            k_bstart<double><<<U, NT, 0, st>>>(s->ln[0].d_sys, s->ln[0].d_unit_sys, s->ln[0].d_partials, s->d_mask);
         }
         GB_CHECK_CUDA(cudaGetLastError());
     }
@@ -646,15 +674,19 @@ static void server_loop(gb_server *s) {
                 continue;
             }
         }
-        // A. launch a chunk of CG iterations for the iterating slots (main stream)
+        // A. launch a chunk of CG iterations for the iterating slots of each
+        // lane (the lane's stream; the two lanes' chunks run side by side)
         gb::Range round_range("gbpcg:serve_round");
-        std::vector<Slot *> it_slots;
-        for (auto &p : s->slots) if (p->state == SL_ITER) it_slots.push_back(p.get());
-        // the table in width-class order: each class's units are contiguous
-        std::stable_sort(it_slots.begin(), it_slots.end(),
-                         [](const Slot *a, const Slot *b) { return width_class(a->k) < width_class(b->k); });
-        bool launched = false;
-        if (!it_slots.empty()) {
+        std::vector<Slot *> lane_slots[gb_server::NLANES];
+        for (auto &p : s->slots) if (p->state == SL_ITER) lane_slots[p->lane].push_back(p.get());
+        bool launched[gb_server::NLANES] = {};
+        for (int li = 0; li < gb_server::NLANES && s->fatal == GB_OK; ++li) {
+            std::vector<Slot *> &it_slots = lane_slots[li];
+            gb_server::Lane &Ln = s->ln[li];
+            if (it_slots.empty()) continue;
+            // the table in width-class order: each class's units are contiguous
+            std::stable_sort(it_slots.begin(), it_slots.end(),
+                             [](const Slot *a, const Slot *b) { return width_class(a->k) < width_class(b->k); });
             std::vector<BSys> tab;
             std::vector<int> umap;
             ClassRanges cls;
@@ -667,43 +699,44 @@ static void server_loop(gb_server *s) {
                 cls.count[c] = (int)umap.size() - cls.base[c];
             }
             for (int c = 0; c < ClassRanges::N; ++c) if (cls.base[c] < 0) cls.base[c] = 0;
-            int rc = grow(s, &s->d_unit_sys, &s->cap_umap, umap.size(), s->main_st);
-            if (rc == GB_OK) rc = grow(s, &s->d_partials, &s->cap_part, umap.size() * 3 * KMAX, s->main_st);
+            int rc = grow(s, &Ln.d_unit_sys, &Ln.cap_umap, umap.size(), Ln.st);
+            if (rc == GB_OK) rc = grow(s, &Ln.d_partials, &Ln.cap_part, umap.size() * 3 * KMAX, Ln.st);
             BGlobal g{};
             g.maxit = s->opt.max_iter;
             g.active_systems = (int)it_slots.size();
             g.stop_on_retire = 1;
             const bool adaptive = s->opt.iters_per_step <= 0;
-            const int ips = adaptive ? s->ips : s->opt.iters_per_step;
+            const int ips = adaptive ? Ln.ips : s->opt.iters_per_step;
             g.budget = ips;
-            cudaError_t e = cudaMemcpyAsync(s->d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, s->main_st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, s->main_st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_G, &g, sizeof(g), cudaMemcpyHostToDevice, s->main_st);
+            cudaError_t e = cudaMemcpyAsync(Ln.d_sys, tab.data(), sizeof(BSys) * tab.size(), cudaMemcpyHostToDevice, Ln.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(Ln.d_unit_sys, umap.data(), sizeof(int) * umap.size(), cudaMemcpyHostToDevice, Ln.st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(Ln.d_G, &g, sizeof(g), cudaMemcpyHostToDevice, Ln.st);
             const int U = (int)umap.size();
-            if (e == cudaSuccess && adaptive) e = cudaEventRecord(s->ev0, s->main_st);
+            if (e == cudaSuccess && adaptive) e = cudaEventRecord(Ln.ev0, Ln.st);
             for (int i = 0; i < ips && e == cudaSuccess && rc == GB_OK; ++i) {
                 ::gb::count_launches(2);
                 if (ru) {
-                    launch_bspmm<float, float>(true, cls, U, s->d_sys, s->d_unit_sys, s->d_G, s->d_partials, s->main_st);
-                    k_bupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
-                    k_bpupdate<float><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
+                    launch_bspmm<float, float>(true, cls, U, Ln.d_sys, Ln.d_unit_sys, Ln.d_G, Ln.d_partials, Ln.st);
+                    k_bupdate<float><<<U, NT, 0, Ln.st>>>(Ln.d_sys, Ln.d_unit_sys, Ln.d_G, Ln.d_partials);
+                    k_bpupdate<float><<<U, NT, 0, Ln.st>>>(Ln.d_sys, Ln.d_unit_sys, Ln.d_G);
                 } else {
-                    launch_bspmm<double, double>(true, cls, U, s->d_sys, s->d_unit_sys, s->d_G, s->d_partials, s->main_st);
-                    k_bupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G, s->d_partials);
-                    k_bpupdate<double><<<U, NT, 0, s->main_st>>>(s->d_sys, s->d_unit_sys, s->d_G);
+                    launch_bspmm<double, double>(true, cls, U, Ln.d_sys, Ln.d_unit_sys, Ln.d_G, Ln.d_partials, Ln.st);
+                    k_bupdate<double><<<U, NT, 0, Ln.st>>>(Ln.d_sys, Ln.d_unit_sys, Ln.d_G, Ln.d_partials);
+                    k_bpupdate<double><<<U, NT, 0, Ln.st>>>(Ln.d_sys, Ln.d_unit_sys, Ln.d_G);
                 }
             }
             if (e == cudaSuccess) e = cudaGetLastError();
-            if (e == cudaSuccess && adaptive) e = cudaEventRecord(s->ev1, s->main_st);
-            if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->main_st);
+            if (e == cudaSuccess && adaptive) e = cudaEventRecord(Ln.ev1, Ln.st);
+            if (e == cudaSuccess) e = cudaEventRecord(Ln.ev, Ln.st);
             if (e != cudaSuccess || rc != GB_OK) {
                 s->fatal = e != cudaSuccess ? GB_ECUDA : rc;
                 s->fatal_msg = e != cudaSuccess ? cudaGetErrorString(e) : gbpcg_last_error();
                 break;
             }
-            launched = true;
+            launched[li] = true;
             s->stats.steps += 1;
         }
+        if (s->fatal != GB_OK) break;
         // B. admit while the chunk runs (side stream)
         while (!s->pending.empty() && (int)s->slots.size() < s->opt.max_slots) {
             SReq &q = s->pending.front();
@@ -735,25 +768,27 @@ static void server_loop(gb_server *s) {
             const int rc = launch_persistent(s);
             if (rc != GB_OK) { s->fatal = rc; s->fatal_msg = gbpcg_last_error(); break; }
         }
-        // C. wait for the chunk, pull the column states of the slots in it
-        if (launched) {
-            cudaError_t e = cudaEventSynchronize(s->ev);
+        // C. wait for each lane's chunk, pull the column states of its slots
+        for (int li = 0; li < gb_server::NLANES && s->fatal == GB_OK; ++li) {
+            if (!launched[li]) continue;
+            gb_server::Lane &Ln = s->ln[li];
+            cudaError_t e = cudaEventSynchronize(Ln.ev);
             if (e == cudaSuccess && s->opt.iters_per_step <= 0) {
                 // adaptive chunk length: about CHUNK_MS of iterations of the
-                // current resident set per chunk, so that arrivals are admitted
+                // lane's resident set per chunk, so that arrivals are admitted
                 // (and small requests solved) within about that long
                 BGlobal hg{};
                 float ms = 0.f;
-                e = cudaMemcpy(&hg, s->d_G, sizeof(hg), cudaMemcpyDeviceToHost);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->ev0, s->ev1);
-                const int done_its = std::max(1, s->ips - std::max(0, hg.budget));
+                e = cudaMemcpy(&hg, Ln.d_G, sizeof(hg), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, Ln.ev0, Ln.ev1);
+                const int done_its = std::max(1, Ln.ips - std::max(0, hg.budget));
                 if (e == cudaSuccess && ms > 0.f) {
                     const double per_it = (double)ms / done_its;
                     const double want = CHUNK_MS / std::max(per_it, 1e-3);
-                    s->ips = (int)std::max(4.0, std::min(200.0, want));
+                    Ln.ips = (int)std::max(4.0, std::min(200.0, want));
                 }
             }
-            for (Slot *L : it_slots) {
+            for (Slot *L : lane_slots[li]) {
                 if (e != cudaSuccess) break;
                 std::vector<int> done(L->k);
                 e = cudaMemcpy(done.data(), L->c.done, sizeof(int) * L->k, cudaMemcpyDeviceToHost);
@@ -762,15 +797,17 @@ static void server_loop(gb_server *s) {
                 L->active = a;
                 if (a == 0) L->state = SL_SERVICE;
             }
-            if (e != cudaSuccess) { s->fatal = GB_ECUDA; s->fatal_msg = cudaGetErrorString(e); break; }
+            if (e != cudaSuccess) { s->fatal = GB_ECUDA; s->fatal_msg = cudaGetErrorString(e); }
         }
+        if (s->fatal != GB_OK) break;
+        const bool any_launched = launched[0] || launched[1];
         // C'. persistent launches that have finished
         bool pdone = false;
         {
             const int rc = poll_persistent(s, &pdone);
             if (rc != GB_OK) { s->fatal = rc; s->fatal_msg = gbpcg_last_error(); break; }
         }
-        if (!launched && !pdone && !s->plaunch.empty()) {
+        if (!any_launched && !pdone && !s->plaunch.empty()) {
             // only persistent launches in flight: poll them gently
             bool serviceable = false;
             for (auto &p : s->slots) serviceable |= p->state == SL_SERVICE;
@@ -792,7 +829,7 @@ static void server_loop(gb_server *s) {
     }
     // fatal error or stop: fail whatever is left (after any persistent launch
     // still using the slots' buffers has finished)
-    cudaStreamSynchronize(s->main_st);
+    for (auto &Ln : s->ln) cudaStreamSynchronize(Ln.st);
     for (auto &L : s->plaunch) {
         cudaStreamSynchronize(L->st);
         cudaFreeAsync(L->d_tab, L->st);
@@ -806,17 +843,20 @@ static void server_loop(gb_server *s) {
     for (auto &q : s->pending) finish(s, q, s->fatal ? s->fatal : GB_EINVAL, nullptr);
     s->pending.clear();
     cudaStreamSynchronize(s->side_st);
-    cudaStreamSynchronize(s->main_st);
+    for (auto &Ln : s->ln) cudaStreamSynchronize(Ln.st);
 }
 
 // ================================================================= ABI ==
 // Releases what serve_create made of a server whose thread never started.
 static void release_unstarted(gb_server *s) {
-    cudaFree(s->d_sys); cudaFree(s->d_mask); cudaFree(s->d_G); cudaFree(s->d_sys1); cudaFree(s->d_mask1);
-    if (s->ev) cudaEventDestroy(s->ev);
-    if (s->ev0) cudaEventDestroy(s->ev0);
-    if (s->ev1) cudaEventDestroy(s->ev1);
-    if (s->main_st) cudaStreamDestroy(s->main_st);
+    for (auto &Ln : s->ln) {
+        cudaFree(Ln.d_sys); cudaFree(Ln.d_G);
+        if (Ln.ev) cudaEventDestroy(Ln.ev);
+        if (Ln.ev0) cudaEventDestroy(Ln.ev0);
+        if (Ln.ev1) cudaEventDestroy(Ln.ev1);
+        if (Ln.st) cudaStreamDestroy(Ln.st);
+    }
+    cudaFree(s->d_mask); cudaFree(s->d_sys1); cudaFree(s->d_mask1);
     if (s->side_st) cudaStreamDestroy(s->side_st);
     delete s;
 }
@@ -845,14 +885,17 @@ extern "C" int serve_create(const ServeOptions *opt, const gb_allocator *alloc, 
 #define GB_SC(expr) if (e == cudaSuccess && (e = (expr)) != cudaSuccess) what = #expr
     if (opt->device >= 0) GB_SC(cudaSetDevice(opt->device));
     GB_SC(cudaGetDevice(&s->dev));
-    GB_SC(cudaStreamCreateWithFlags(&s->main_st, cudaStreamNonBlocking));
+    for (int li = 0; li < gb_server::NLANES; ++li) {
+        gb_server::Lane &Ln = s->ln[li];
+        GB_SC(cudaStreamCreateWithFlags(&Ln.st, cudaStreamNonBlocking));
+        GB_SC(cudaEventCreateWithFlags(&Ln.ev, cudaEventDisableTiming));
+        GB_SC(cudaEventCreate(&Ln.ev0));
+        GB_SC(cudaEventCreate(&Ln.ev1));
+        GB_SC(cudaMalloc((void **)&Ln.d_sys, sizeof(BSys) * s->opt.max_slots));
+        GB_SC(cudaMalloc((void **)&Ln.d_G, sizeof(BGlobal)));
+    }
     GB_SC(cudaStreamCreateWithFlags(&s->side_st, cudaStreamNonBlocking));
-    GB_SC(cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming));
-    GB_SC(cudaEventCreate(&s->ev0));
-    GB_SC(cudaEventCreate(&s->ev1));
-    GB_SC(cudaMalloc((void **)&s->d_sys, sizeof(BSys) * s->opt.max_slots));
     GB_SC(cudaMalloc((void **)&s->d_mask, sizeof(int) * KMAX * s->opt.max_slots));
-    GB_SC(cudaMalloc((void **)&s->d_G, sizeof(BGlobal)));
     GB_SC(cudaMalloc((void **)&s->d_sys1, sizeof(BSys)));
     GB_SC(cudaMalloc((void **)&s->d_mask1, sizeof(int) * KMAX));
 #undef GB_SC
@@ -921,12 +964,15 @@ extern "C" void serve_destroy(gb_server *s) {
         s->cv.notify_all();
     }
     if (s->th.joinable()) s->th.join();
-    cudaFree(s->d_sys); cudaFree(s->d_unit_sys); cudaFree(s->d_mask); cudaFree(s->d_G); cudaFree(s->d_partials);
+    for (auto &Ln : s->ln) {
+        cudaFree(Ln.d_sys); cudaFree(Ln.d_unit_sys); cudaFree(Ln.d_G); cudaFree(Ln.d_partials);
+        cudaEventDestroy(Ln.ev);
+        cudaEventDestroy(Ln.ev0);
+        cudaEventDestroy(Ln.ev1);
+        cudaStreamDestroy(Ln.st);
+    }
+    cudaFree(s->d_mask);
     cudaFree(s->d_sys1); cudaFree(s->d_unit1); cudaFree(s->d_mask1); cudaFree(s->d_partials1);
-    cudaEventDestroy(s->ev);
-    cudaEventDestroy(s->ev0);
-    cudaEventDestroy(s->ev1);
-    cudaStreamDestroy(s->main_st);
     cudaStreamDestroy(s->side_st);
     delete s;
 }
