@@ -67,7 +67,7 @@ def parse():
                     help="skip the full cfg4 solve (32 right-hand sides on 2048^2 P2, fp32 recurrences with fp64 "
                          "reliable updates)")
     ap.add_argument("--profile-kernels", default=None, metavar="SYSTEM",
-                    help="profiling driver only: p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
+                    help="profiling driver only: cfg1|p1|p2|3dp1|3dp2; times the CG kernels with CUDA events")
     ap.add_argument("--profile-precision", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--sweep", default=None, choices=["eps", "rhs", "precond", "degree"],
                     help="accuracy vs stopping tolerance (eps), solve time vs number of right-hand sides (rhs), "
@@ -75,9 +75,10 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-bj", type=int, default=0, metavar="BS",
                     help="profiling driver: time the block-Jacobi iteration with blocks of BS rows")
-    ap.add_argument("--profile-solve", default=None, choices=["bicgstab", "blockcg"],
+    ap.add_argument("--profile-solve", default=None, choices=["bicgstab", "blockcg", "persistent"],
                     help="profiling driver: one solve of the profile system with direct launches (BiCGSTAB, or "
-                         "block CG with --profile-rhs columns)")
+                         "block CG with --profile-rhs columns), or fp64 CG in one persistent launch (persistent: "
+                         "one cluster for n <= 8192, else a grid-tier group)")
     ap.add_argument("--profile-rhs", type=int, default=0, metavar="K",
                     help="profiling driver: time the blocked multi-RHS iteration with K harmonic right-hand sides")
     return ap.parse_args()
@@ -480,7 +481,7 @@ def run_reference(args, rank, world):
     }
 
 
-PROFILE_SYSTEMS = {"p1": (2, 1, 1024, 1, 1, 1, 1), "p2": (2, 2, 1024, 1, 1, 1, 1),
+PROFILE_SYSTEMS = {"cfg1": (2, 1, 64, 0, 0, 0, 0), "p1": (2, 1, 1024, 1, 1, 1, 1), "p2": (2, 2, 1024, 1, 1, 1, 1),
                    "3dp1": (3, 1, 128, 0, 0, 0, 2), "3dp2": (3, 2, 64, 0, 0, 0, 2)}
 
 
@@ -493,6 +494,13 @@ def run_profile(args):
     d = P.FemSystem(dim, deg, cells, jit, dm, seed)
     A = d.to_sell(32, 256, P.GB_VAL_F64 | P.GB_VAL_F32 | P.GB_VAL_BF16)
     prec = {"f64": P.GB_F64, "f32": P.GB_F32_IR, "bf16": P.GB_BF16_IR}[args.profile_precision]
+    if args.profile_solve == "persistent":
+        b = d.lift(d.dirichlet(gid))[:, 0]
+        x, st = A.solve(b, tol=1e-10, persist_off=0 if A.n <= 8192 else 3, raise_on_fail=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"system": args.profile_kernels, "solve": "persistent", "n": A.n,
+                          "iterations": st["iterations"], "solve_ms": st["solve_ms"]}))
+        return
     if args.profile_solve == "bicgstab":
         b = d.lift(d.dirichlet(gid))[:, 0]
         x, st = A.solve(b, tol=1e-10, method=P.GB_BICGSTAB, use_graph=0, max_iter=args.profile_iters,
