@@ -720,12 +720,13 @@ template <class TX> int grid_resident_blocks() {
 
 // Blocks per group for n rows with kp columns each: about one block per
 // GB_GRID_ROWS row-columns, rounded up to a power of two and at most the
-// largest power of two the device holds.  A system's group size, and with it
-// the order of its sums, depends on its own size only.
+// largest power of two the device holds (and at most PNT: one polling thread
+// per block of the group).  A system's group size, and with it the order of
+// its sums, depends on its own size only.
 inline int grid_blocks_for(int64_t n, int kp, int resident) {
     const int64_t want = (n * kp + GB_GRID_ROWS - 1) / GB_GRID_ROWS;
     int64_t cap = 1;
-    while (cap * 2 <= resident) cap *= 2;
+    while (cap * 2 <= resident && cap * 2 <= PNT) cap *= 2;
     int64_t g = 1;
     while (g < want && g < cap) g *= 2;
     return (int)g;
