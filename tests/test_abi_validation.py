@@ -60,3 +60,9 @@ def test_wait_selftest_rejects_bad_limits(G):
     waited = C.c_double(0)
     _einval(G, G.lib().gbpcg_wait_selftest(0.0, None, C.byref(waited)), "limit_ms")
     _einval(G, G.lib().gbpcg_wait_selftest(5000.0, None, C.byref(waited)), "limit_ms")
+
+
+def test_grid_wait_selftest_rejects_bad_limits(G):
+    waited = C.c_double(0)
+    _einval(G, G.lib().gbpcg_grid_wait_selftest(0.0, None, C.byref(waited)), "limit_ms")
+    _einval(G, G.lib().gbpcg_grid_wait_selftest(2500.0, None, C.byref(waited)), "limit_ms")
