@@ -271,9 +271,10 @@ static int serve_persist_tier(int64_t n, int k, bool ru, bool cluster_lane) {
 // Lock-step lane of a request: medium requests (n k2 <= 2^GB_SERVE_MEDIUM_LOG2)
 // iterate in lane 1, larger ones in lane 0, each lane in launches of its own
 // on its own stream, so a medium request advances at the pace of the medium
-// requests' iterations rather than the largest requests' (cfg5 mix, 160
-// requests: medium requests waited 16 x their one-at-a-time time at the
-// median with a single lane).
+// requests' iterations rather than the largest requests' (160 seeded
+// requests of 2D/3D P1/P2 meshes with 1-8 right-hand sides: medium requests
+// waited 16 x their one-at-a-time time at the median with a single lane,
+// 7.5 x with two).
 #ifndef GB_SERVE_MEDIUM_LOG2
 #define GB_SERVE_MEDIUM_LOG2 20
 #endif
